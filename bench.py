@@ -1,0 +1,406 @@
+"""Benchmark: batched edge validation on one or more GB300s.
+
+A step validates one batch of synthetic edges end to end through the C ABI
+(count -> raked interpolation -> FK -> coarse/fine/self checks -> verdict).
+The default workload is the 8-DoF torso arm (100 spheres, 9 link spheres,
+200 self pairs) against 60 oriented cuboids + 20 capsules, 1,000,000 edges
+at 1/32 rad.  `value` is covered states/s (sum of the edges' state counts
+per second) with inputs resident in HBM; `e2e` is the same metric through
+pinned host buffers with the copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode plain|batched]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import vpgen  # noqa: E402
+
+METRIC = "states/s and edges/s validated (batched vs plain, exact verdicts); grads/s"
+UNIT = "states/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# FLOP model (FMA = 2 flops; compares, min/max and sin/cos are not counted):
+# the arithmetic each unit of work performs in the kernel's formulation.
+FLOPS_INTERP_PER_JOINT = 2        # q0 + t dq
+FLOPS_JOINT_TRANSLATE = 18        # p += R t (9 FMA)
+FLOPS_JOINT_ROT_CANONICAL = 18    # two columns rotated (6 FMUL + 6 FFMA)
+FLOPS_JOINT_ROT_GENERAL = 72      # Rodrigues matrix (18) + 3x3 product (54)
+FLOPS_JOINT_PRISMATIC = 21        # axis * q (3) + p += R a (18)
+FLOPS_CENTRE = 18                 # R c + p (9 FMA)
+FLOPS_TEST = {"sphere": 10, "capsule": 22, "cuboid": 26}  # squared-distance ball tests
+FLOPS_PAIR_COARSE = 10            # link centres already posed
+FLOPS_PAIR_FINE = 2 * FLOPS_CENTRE + 10
+
+
+def _git_rev():
+    try:
+        return subprocess.run(["git", "-C", ROOT, "rev-parse", "--short", "HEAD"], capture_output=True,
+                              text=True).stdout.strip() or None
+    except Exception:
+        return None
+
+
+def state_flops(robot) -> float:
+    """FLOPs to pose one state (interpolation + FK over every joint)."""
+    f = FLOPS_INTERP_PER_JOINT * robot.dof
+    for j in range(robot.dof):
+        f += FLOPS_JOINT_TRANSLATE
+        if robot.joint_type[j] == vpgen.PRISMATIC:
+            f += FLOPS_JOINT_PRISMATIC
+        else:
+            ax = np.asarray(robot.joint_axis[j])
+            canonical = np.count_nonzero(ax) == 1 and ax.max() == 1.0
+            f += FLOPS_JOINT_ROT_CANONICAL if canonical else FLOPS_JOINT_ROT_GENERAL
+    return f
+
+
+def work_flops(work, robot) -> float:
+    from paper_2309_14545_gb300 import vp
+    w = [int(x) for x in work]
+    f = w[vp.VP_WORK_STATES] * state_flops(robot)
+    f += w[vp.VP_WORK_LINK_CENTRES] * FLOPS_CENTRE
+    f += w[vp.VP_WORK_COARSE_SPHERE] * FLOPS_TEST["sphere"]
+    f += w[vp.VP_WORK_COARSE_CAPSULE] * FLOPS_TEST["capsule"]
+    f += w[vp.VP_WORK_COARSE_CUBOID] * FLOPS_TEST["cuboid"]
+    f += w[vp.VP_WORK_FINE_SPHERE] * (FLOPS_CENTRE + FLOPS_TEST["sphere"])
+    f += w[vp.VP_WORK_FINE_CAPSULE] * (FLOPS_CENTRE + FLOPS_TEST["capsule"])
+    f += w[vp.VP_WORK_FINE_CUBOID] * (FLOPS_CENTRE + FLOPS_TEST["cuboid"])
+    f += w[vp.VP_WORK_PAIR_COARSE] * FLOPS_PAIR_COARSE
+    f += w[vp.VP_WORK_PAIR_FINE] * FLOPS_PAIR_FINE
+    return float(f)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle leg (CPU)
+
+
+def oracle_rate(w, budget_s=12.0, threads=None, min_edges=64):
+    """The oracle's verdict-only edge validation, as it stands, on all host
+    cores: a bounded prefix of the workload sized to about ``budget_s``.
+    Returns (covered states/s, sample description, cores, seconds)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    o = oracle.Oracle(w.robot, w.env)
+    counts_all = w.counts
+    # calibrate on a small prefix, then size the sample
+    n = min(w.q0.shape[0], max(min_edges, 4 * threads))
+    t = time.perf_counter()
+    o.validate_edges(w.q0[:n], w.q1[:n], None if counts_all is None else counts_all[:n], w.res, n_threads=threads)
+    dt = time.perf_counter() - t
+    n_full = int(min(w.q0.shape[0], max(n, n * budget_s / max(dt, 1e-3))))
+    sl = slice(0, n_full)
+    c = None if counts_all is None else counts_all[sl]
+    t = time.perf_counter()
+    o.validate_edges(w.q0[sl], w.q1[sl], c, w.res, n_threads=threads)
+    dt = time.perf_counter() - t
+    k = c if c is not None else o.edge_count(w.q0[sl], w.q1[sl], w.res)
+    states = float(np.sum(np.maximum(k, 0)))
+    return states / dt, f"first {n_full} edges of {w.name} (verdict mode, linear order, early exit)", threads, dt
+
+
+# ---------------------------------------------------------------------------
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--edges", type=int, default=None, help="override the workload's edge count")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config_block(w, args, world):
+    return {"workload": vpgen.DESCRIPTION.get(args.config, w.name), "config_index": args.config,
+            "edges_per_gpu": int(w.q0.shape[0]), "dof": w.robot.dof, "spheres": w.robot.n_spheres,
+            "self_pairs": int(len(w.robot.self_pairs)), "primitives": w.env.n_prims,
+            "resolution": float(w.res), "explicit_counts": w.counts is not None,
+            "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas x{world}"}
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    w = vpgen.workload(args.config, n_edges=args.edges)
+    times = []
+    rate = None
+    for i in range(args.warmup + args.steps):
+        r, sample, cores, dt = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+        if i >= args.warmup:
+            times.append(dt)
+            rate = r if rate is None else rate
+    value = float(rate)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(w, args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2309_14545_gb300 import Validator, vp
+
+    # each rank validates its own seeded batch of the same size (weak scaling)
+    base = vpgen.workload(args.config, n_edges=args.edges)
+    if world > 1 and rank > 0:
+        q0, q1 = vpgen.uniform_edges(base.robot, base.q0.shape[0], seed=200 + args.config + 1000 * rank)
+        counts = None if base.counts is None else vpgen.loguniform_counts(base.q0.shape[0], 200 + args.config + 1000 * rank)
+        w = vpgen.Workload(base.name, base.robot, base.env, q0, q1, counts, base.res)
+    else:
+        w = base
+    E = w.q0.shape[0]
+    val = Validator(w.robot, w.env, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    mode = vp.VP_MODE_BATCHED if args.mode == "batched" else vp.VP_MODE_PLAIN
+    with torch.cuda.stream(stream):
+        q0 = torch.from_numpy(w.q0).to(dev)
+        q1 = torch.from_numpy(w.q1).to(dev)
+        counts = None if w.counts is None else torch.from_numpy(w.counts).to(dev)
+        valid = torch.empty(E, dtype=torch.uint8, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        k = counts if counts is not None else val.edge_counts(q0, q1, w.res, stream=stream)
+        covered = float(k.to(torch.int64).clamp(min=0).sum().item())
+        if mode == vp.VP_MODE_BATCHED:
+            val.autotune(q0, q1, counts, w.res, stream=stream)
+        # work counters (untimed): the FLOP numerator of the roofline
+        _, work = val.validate_edges_work(q0, q1, counts, w.res, stream=stream)
+        work = work.cpu().numpy()
+    flops = work_flops(work, w.robot)
+
+    def step(s_out):
+        val.validate_edges(q0, q1, counts, w.res, mode=mode, stream=stream, out=s_out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(valid)
+    st, bits = val.sync_status(stream)
+    if st != vp.VP_OK:
+        raise RuntimeError(f"device status {st} bits {bits:#x}")
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(valid)
+            b.record(stream)
+            evs.append((a, b))
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = float(np.mean(ms))
+
+    # e2e: pinned host buffers, copies inside the timed region
+    hq0 = torch.from_numpy(w.q0).pin_memory()
+    hq1 = torch.from_numpy(w.q1).pin_memory()
+    hc = None if w.counts is None else torch.from_numpy(w.counts).pin_memory()
+    hv = torch.empty(E, dtype=torch.uint8).pin_memory()
+    dq0, dq1 = torch.empty_like(q0), torch.empty_like(q1)
+    dc = None if counts is None else torch.empty_like(counts)
+    h2d = 2 * w.q0.nbytes + (0 if w.counts is None else w.counts.nbytes)
+    d2h = E
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dq0.copy_(hq0, non_blocking=True)
+            dq1.copy_(hq1, non_blocking=True)
+            if dc is not None:
+                dc.copy_(hc, non_blocking=True)
+            val.validate_edges(dq0, dq1, dc, w.res, mode=mode, stream=stream, out=valid)
+            hv.copy_(valid, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if i >= args.warmup:
+                e2e_ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    st, bits = val.sync_status(stream)
+    if st != vp.VP_OK:
+        raise RuntimeError(f"device status {st} bits {bits:#x}")
+
+    t_max = ms_step
+    e2e_step = float(np.mean(e2e_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step, e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, e2e_step = float(t[0]), float(t[1])
+        c = torch.tensor([covered, float(E)], dtype=torch.float64, device=dev)
+        dist.all_reduce(c)
+        covered_all, edges_all = float(c[0]), float(c[1])
+    else:
+        covered_all, edges_all = covered, float(E)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    value = covered_all / (t_max / 1000.0)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = 2 * 128 * n_sm * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+    achieved = flops / (ms_step / 1000.0) / 1e12
+    valid_frac = float(valid.float().mean().item())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_block(w, args, world),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": _traffic(args, E),
+                     "peak_basis": f"FP32 FMA: 128 lanes x 2 flops x {n_sm} SMs x {sm_max:.0f} MHz (derived)",
+                     "kernel": "edges_plain_kernel" if mode == vp.VP_MODE_PLAIN else "edges_batched_kernel",
+                     "flops_per_step": flops},
+        "e2e": {"value": covered_all / (e2e_step / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "gpu_launches": args.steps * 1,
+        "clocks": clocks,
+        "extra": {"mode": args.mode, "edges_per_s": edges_all / (t_max / 1000.0),
+                  "evaluated_states_per_s": world * int(work[vp.VP_WORK_STATES]) / (t_max / 1000.0),
+                  "covered_states_per_step": covered_all, "valid_edge_fraction": valid_frac,
+                  "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
+    }
+    if not args.no_cpu_baseline:
+        r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _traffic(args, E):
+    """DRAM bytes per launch from the committed ncu summary, only if it was
+    taken on the current kernel sources (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        from paper_2309_14545_gb300 import build
+        if rec.get("sources_hash") != build.sources_hash():
+            return None
+        ent = rec.get(f"config{args.config}")
+        if not ent:
+            return None
+        return float(ent["dram_bytes_per_launch"]) * E / float(ent["edges"])
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * vp.h -- C ABI of libvp: batched motion (edge) validation on one GPU.
+ *
+ * Method: Thomason, Kingston, Kavraki, "Motions in Microseconds via Vectorized
+ * Sampling-Based Planning" (arXiv 2309.14545), Sec. III ("Method"):
+ *   - a state validity function and an edge validity function over a robot
+ *     in an environment (Sec. III, first paragraph);
+ *   - forward kinematics that poses many configurations at once and computes
+ *     only collision-sphere positions (Sec. III-B, III-C);
+ *   - collision checks of robot spheres against sphere / capsule / cuboid
+ *     primitives and robot self pairs (Sec. III-C);
+ *   - the "raked" edge validator: spatially spread states checked together,
+ *     a per-link bounding-sphere "mid-phase", checks interleaved with FK, and
+ *     termination at the first collision (Sec. III-D, Fig. 2);
+ *   - linear interpolation between configurations in a Euclidean C-space
+ *     (Sec. III-E).
+ *
+ * Conventions for every call
+ *   - Every function returns a vp_status and never aborts the process.
+ *   - Argument errors are detected on the host before anything is launched
+ *     (VP_ERR_ARG / VP_ERR_CAPACITY / VP_ERR_NOT_LOADED); the message is in
+ *     vp_last_error(ctx).
+ *   - Problems only visible on the device (an explicit state count < 2, an
+ *     edge longer than VP_MAX_STEPS steps, a watchdog timeout) set bits in a
+ *     device status word; vp_sync_status() synchronises, reads and clears it.
+ *     Such an edge is reported invalid.
+ *   - Pointers named "device" are CUDA device pointers (e.g. a torch tensor's
+ *     data_ptr()) on the context's device; the caller owns them and keeps
+ *     them alive until the work on `stream` completes.  `stream` is a
+ *     cudaStream_t (NULL = the legacy default stream); compute calls are
+ *     asynchronous with respect to the host.
+ *   - Host descriptors passed to the loaders are copied; the caller keeps
+ *     ownership.
+ *   - Configurations are float32, row-major [n, D] with D = the robot's joint
+ *     count.  Lengths in metres, angles in radians.
+ *   - A configuration with a non-finite coordinate is invalid; an edge with a
+ *     non-finite endpoint coordinate is invalid.  Joint limits are a property
+ *     of the workload, not a check: out-of-limit configurations are validated
+ *     as given.
+ *   - A vp_ctx is not thread-safe; distinct contexts are independent.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vp_ctx vp_ctx;
+
+typedef enum {
+    VP_OK = 0,
+    VP_ERR_ARG = 1,        /* invalid argument; nothing was launched            */
+    VP_ERR_CUDA = 2,       /* a CUDA runtime call failed                         */
+    VP_ERR_CAPACITY = 3,   /* robot or environment beyond a compiled limit       */
+    VP_ERR_NOT_LOADED = 4, /* robot or environment not loaded                    */
+    VP_ERR_TIMEOUT = 5,    /* a device watchdog gave up (work left unfinished)   */
+    VP_ERR_DEVICE = 6      /* bad input found on the device (see vp_sync_status) */
+} vp_status;
+
+enum { VP_JOINT_REVOLUTE = 0, VP_JOINT_PRISMATIC = 1 };
+
+/* vp_validate_edges modes. */
+enum {
+    VP_MODE_PLAIN = 0,    /* one launch, one warp per edge, fixed tiling          */
+    VP_MODE_BATCHED = 1,  /* persistent length-bucketed work queue, tuned tiling  */
+    VP_MODE_PER_EDGE = 2  /* one plain launch per edge (the literal baseline)     */
+};
+
+/* Compiled limits. */
+#define VP_MAX_JOINTS 16
+#define VP_MAX_SPHERES 256
+#define VP_MAX_PAIRS 1024
+#define VP_MAX_ENV_BYTES (160 * 1024) /* packed environment held in shared memory */
+#define VP_MAX_STEPS 16777216         /* longest edge, in resolution steps        */
+
+/* Device status bits (OR-ed into the status word). */
+#define VP_DEVERR_COUNT 0x1u   /* an explicit count < 2                    */
+#define VP_DEVERR_LENGTH 0x2u  /* an edge longer than VP_MAX_STEPS steps   */
+#define VP_DEVERR_TIMEOUT 0x4u /* the persistent kernel's watchdog fired   */
+
+/*
+ * Robot: a forest of joint chains on a fixed base (host memory, copied).
+ *   joint_parent[j]  -1 (the base) or an earlier joint index.
+ *   joint_type[j]    VP_JOINT_REVOLUTE / VP_JOINT_PRISMATIC.
+ *   joint_axis       [D][3] unit axis in the joint's frame.
+ *   joint_origin     [D][3][4] fixed [R | t] from the parent's frame to the
+ *                    joint's frame, row-major.
+ *   Link 0 is the base; link j+1 is the frame after joint j moved by q_j:
+ *   T_{j+1} = T_{parent(j)+1} * origin_j * (Rot(axis_j, q_j) or Trans(axis_j q_j)).
+ *   sphere_link[s], sphere_centre [S][3] (in the link's frame), sphere_radius[s].
+ *   link_spheres     [D+1][4] conservative bounding sphere per link (centre in
+ *                    the link frame, radius; radius <= 0 for a link with no
+ *                    spheres), or NULL to derive them (centre = mean of the
+ *                    link's sphere centres, radius = max |c_s - c| + r_s).
+ *                    Given spheres must contain every sphere of their link
+ *                    (else VP_ERR_ARG).  The paper's "mid-phase" (Sec. III-D).
+ *   self_pairs       [P][2] sphere indices checked against each other.
+ */
+typedef struct {
+    int32_t n_joints;
+    const int32_t *joint_parent;
+    const int32_t *joint_type;
+    const double *joint_axis;
+    const double *joint_origin;
+    int32_t n_spheres;
+    const int32_t *sphere_link;
+    const double *sphere_centre;
+    const double *sphere_radius;
+    const double *link_spheres;
+    int32_t n_pairs;
+    const int32_t *self_pairs;
+} vp_robot_desc;
+
+/*
+ * Environment primitives (host memory, copied), Sec. III-C:
+ *   spheres  [n][4]  centre, radius
+ *   capsules [n][7]  segment end p0, end p1, radius
+ *   cuboids  [n][15] centre, R (3x3 row-major; column i = box axis i in the
+ *                    world frame), half-extents
+ */
+typedef struct {
+    int32_t n_spheres;
+    const double *spheres;
+    int32_t n_capsules;
+    const double *capsules;
+    int32_t n_cuboids;
+    const double *cuboids;
+} vp_env_desc;
+
+/* Create a context on CUDA device `device`.  Allocates a small device status
+ * word.  The caller's current device is left unchanged. */
+vp_status vp_create(vp_ctx **out, int device);
+/* Free everything the context owns.  NULL is accepted. */
+vp_status vp_destroy(vp_ctx *ctx);
+/* Message of the last failed call on ctx (valid until the next call). */
+const char *vp_last_error(const vp_ctx *ctx);
+
+/* Load (replace) the robot.  Synchronous.  Errors: VP_ERR_ARG for malformed
+ * tables, VP_ERR_CAPACITY beyond the VP_MAX_* limits. */
+vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *robot);
+/* Load (replace) the environment into a device buffer the context owns.
+ * Synchronous.  VP_ERR_CAPACITY if it packs to more than VP_MAX_ENV_BYTES. */
+vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *env);
+
+/* FK test hook (Sec. III-B): world sphere centres of n configurations.
+ * q: device float [n][D]; centres: device float [n][S][3], spheres in the
+ * robot's original order. */
+vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float *centres, void *stream);
+
+/* State validity (Sec. III-C): valid[i] = 1 iff configuration i collides with
+ * nothing (clearance >= 0 up to float32 rounding).  q: device float [n][D];
+ * valid: device uint8 [n]. */
+vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, uint8_t *valid, void *stream);
+
+/* State counts of edges (test hook for the discretisation, Sec. III-D):
+ * counts[e] = max(2, ceil(max_d |q1_d - q0_d| / resolution) + 1), computed in
+ * float32 with IEEE division; -1 for an edge with a non-finite coordinate or
+ * more than VP_MAX_STEPS steps.  q0, q1: device float [E][D]; counts: device
+ * int32 [E]. */
+vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float resolution,
+                         int64_t n_edges, int32_t *counts, void *stream);
+
+/* Edge validity (Sec. III-D): valid[e] = 1 iff every state
+ * q(t) = q0 + t (q1 - q0), t = i/(k-1), i = 0..k-1, is valid, where k is
+ * counts[e] (device int32 [E], each >= 2) or, with counts == NULL, the count
+ * from `resolution` as in vp_edge_counts.  States are visited in raked order
+ * (a spread set of states per round), each pose is checked link by link
+ * against the bounding-sphere mid-phase, then fine spheres, then self pairs,
+ * and the edge stops at the first collision.  mode: VP_MODE_*.
+ * q0, q1: device float [E][D]; valid: device uint8 [E]. */
+vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                            float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
+
+/* Work counters for the FLOP model: the plain edge validation with counters
+ * of the work done (VP_WORK_* indices) added into `work` (device uint64
+ * [VP_WORK_N]; the caller zeroes it).  Only states of the edge are counted
+ * (a lane parked on a repeated state is not). */
+enum {
+    VP_WORK_STATES = 0,     /* states posed (FK run)                          */
+    VP_WORK_LINK_CENTRES,   /* link bounding-sphere centres computed          */
+    VP_WORK_COARSE_SPHERE,  /* coarse tests, by primitive type                */
+    VP_WORK_COARSE_CAPSULE,
+    VP_WORK_COARSE_CUBOID,
+    VP_WORK_FINE_SPHERE,    /* fine tests (incl. the sphere centre), by type  */
+    VP_WORK_FINE_CAPSULE,
+    VP_WORK_FINE_CUBOID,
+    VP_WORK_PAIR_COARSE,    /* link-pair bounding-sphere tests                */
+    VP_WORK_PAIR_FINE,      /* sphere-pair tests                              */
+    VP_WORK_EDGES_DONE,     /* edges finished                                 */
+    VP_WORK_N = 16
+};
+vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                 float resolution, int64_t n_edges, uint8_t *valid, uint64_t *work,
+                                 void *stream);
+
+/* Penetration cost (an addition beside the paper, which defines none):
+ * cost[i] = sum_s sum_o max(0, r_s + margin - d(c_s, o))^2 over environment
+ * primitives o (d = signed distance, negative inside).  If grad != NULL, the
+ * reverse-mode FK adjoint writes dcost/dq into grad (device float [n][D]).
+ * q: device float [n][D]; cost: device float [n]. */
+vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin, float *cost,
+                            float *grad, void *stream);
+
+/* Tune the batched mode's tiling on a sample of edges (runs kernels and
+ * synchronises `stream`).  The choice is cached in the context per robot,
+ * environment and edge-length profile. */
+vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                      float resolution, int64_t n_edges, void *stream);
+
+/* Synchronise `stream`, read and clear the device status word: VP_OK,
+ * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are
+ * returned in *bits when bits != NULL. */
+vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VP_H */

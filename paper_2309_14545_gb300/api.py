@@ -1,0 +1,101 @@
+"""User-facing wrappers over the C ABI: a context owner and an autograd cost.
+
+Still marshalling only -- every computation happens in libvp's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import vp
+
+
+class Validator:
+    """Owns one vp_ctx with a robot and an environment loaded."""
+
+    def __init__(self, robot, env, device: int = 0):
+        self.device = int(device)
+        self.ctx = vp.vp_create(self.device)
+        self.dof = int(len(robot.joint_type))
+        self.n_spheres = int(len(robot.sphere_radius))
+        try:
+            vp.vp_load_robot(self.ctx, robot)
+            vp.vp_load_env(self.ctx, env)
+        except Exception:
+            vp.vp_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def close(self):
+        if self.ctx is not None:
+            vp.vp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return torch.device("cuda", self.device)
+
+    def load_env(self, env):
+        vp.vp_load_env(self.ctx, env)
+
+    def fk_spheres(self, q, stream=None):
+        out = torch.empty((q.shape[0], self.n_spheres, 3), dtype=torch.float32, device=self._dev())
+        vp.vp_fk_spheres(self.ctx, q, out, stream)
+        return out
+
+    def validate_states(self, q, stream=None):
+        out = torch.empty(q.shape[0], dtype=torch.uint8, device=self._dev())
+        vp.vp_validate_states(self.ctx, q, out, stream)
+        return out
+
+    def edge_counts(self, q0, q1, resolution, stream=None):
+        out = torch.empty(q0.shape[0], dtype=torch.int32, device=self._dev())
+        vp.vp_edge_counts(self.ctx, q0, q1, float(resolution), out, stream)
+        return out
+
+    def validate_edges(self, q0, q1, counts=None, resolution=1.0 / 32.0, mode=vp.VP_MODE_PLAIN, stream=None,
+                       out=None):
+        if out is None:
+            out = torch.empty(q0.shape[0], dtype=torch.uint8, device=self._dev())
+        vp.vp_validate_edges(self.ctx, q0, q1, counts, float(resolution), out, mode, stream)
+        return out
+
+    def validate_edges_work(self, q0, q1, counts=None, resolution=1.0 / 32.0, stream=None):
+        out = torch.empty(q0.shape[0], dtype=torch.uint8, device=self._dev())
+        work = torch.zeros(vp.VP_WORK_N, dtype=torch.int64, device=self._dev())
+        vp.vp_validate_edges_work(self.ctx, q0, q1, counts, float(resolution), out, work, stream)
+        return out, work
+
+    def autotune(self, q0, q1, counts=None, resolution=1.0 / 32.0, stream=None):
+        vp.vp_autotune(self.ctx, q0, q1, counts, float(resolution), stream)
+
+    def collision_cost(self, q, margin, grad=False, stream=None):
+        cost = torch.empty(q.shape[0], dtype=torch.float32, device=self._dev())
+        g = torch.empty_like(q) if grad else None
+        vp.vp_collision_cost(self.ctx, q, float(margin), cost, g, stream)
+        return (cost, g) if grad else cost
+
+    def sync_status(self, stream=None):
+        return vp.vp_sync_status(self.ctx, stream)
+
+
+class CollisionCost(torch.autograd.Function):
+    """c(q) = sum over robot spheres s and primitives o of
+    max(0, r_s + margin - d(c_s, o))^2; backward runs the reverse-mode FK
+    adjoint kernel (forward recomputed, then one backward sweep over joints)."""
+
+    @staticmethod
+    def forward(ctx, q, validator: Validator, margin: float):
+        qc = q.detach().contiguous()
+        cost, grad = validator.collision_cost(qc, margin, grad=True)
+        ctx.save_for_backward(grad)
+        return cost
+
+    @staticmethod
+    def backward(ctx, dcost):
+        (grad,) = ctx.saved_tensors
+        return grad * dcost[:, None], None, None

@@ -1,0 +1,559 @@
+// C ABI of libvp (see include/vp.h): context, robot / environment packing
+// with argument checks, and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vp_batched.h"
+#include "vp_cost.h"
+#include "vp_internal.h"
+
+using namespace vp;
+
+struct vp_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    RobotParams robot{};
+    bool robot_loaded = false;
+    std::vector<uint16_t> sorted_of;  // caller's sphere index -> sorted index
+    float4 *env_buf = nullptr;
+    EnvView env{};
+    bool env_loaded = false;
+    unsigned *status = nullptr;  // device status word
+    BatchedState batched;        // scratch and tuned tiling of the batched mode
+    std::string err;
+};
+
+namespace {
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev_ >= 0) {
+            int cur = -1;
+            cudaGetDevice(&cur);
+            if (cur != prev_) cudaSetDevice(prev_);
+        }
+    }
+
+   private:
+    int prev_ = -1;
+};
+
+vp_status fail(vp_ctx *ctx, vp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return s;
+}
+
+vp_status cuda_fail(vp_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, VP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite_all(const double *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+double norm3(const double *v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+vp_status check_loaded(vp_ctx *ctx) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "robot not loaded");
+    if (!ctx->env_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "environment not loaded");
+    return VP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// lifetime
+
+extern "C" vp_status vp_create(vp_ctx **out, int device) {
+    if (!out) return VP_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return VP_ERR_ARG;
+    vp_ctx *ctx = new vp_ctx();
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, 256);
+    if (e != cudaSuccess) {
+        if (ctx->status) cudaFree(ctx->status);
+        delete ctx;
+        return VP_ERR_CUDA;
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = ctx;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_destroy(vp_ctx *ctx) {
+    if (!ctx) return VP_OK;
+    {
+        DeviceGuard g(ctx->device);
+        if (ctx->env_buf) cudaFree(ctx->env_buf);
+        if (ctx->status) cudaFree(ctx->status);
+        batched_release(ctx->batched);
+    }
+    delete ctx;
+    return VP_OK;
+}
+
+extern "C" const char *vp_last_error(const vp_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------------------
+// robot
+
+extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!r) return fail(ctx, VP_ERR_ARG, "robot descriptor is NULL");
+    const int D = r->n_joints, S = r->n_spheres, P = r->n_pairs;
+    if (D < 1) return fail(ctx, VP_ERR_ARG, "n_joints must be >= 1");
+    if (D > kMaxJoints) return fail(ctx, VP_ERR_CAPACITY, "n_joints %d > %d", D, kMaxJoints);
+    if (S < 0 || P < 0) return fail(ctx, VP_ERR_ARG, "negative sphere or pair count");
+    if (S > kMaxSpheres) return fail(ctx, VP_ERR_CAPACITY, "n_spheres %d > %d", S, kMaxSpheres);
+    if (P > kMaxPairs) return fail(ctx, VP_ERR_CAPACITY, "n_pairs %d > %d", P, kMaxPairs);
+    if (!r->joint_parent || !r->joint_type || !r->joint_axis || !r->joint_origin)
+        return fail(ctx, VP_ERR_ARG, "joint table pointer is NULL");
+    if (S > 0 && (!r->sphere_link || !r->sphere_centre || !r->sphere_radius))
+        return fail(ctx, VP_ERR_ARG, "sphere table pointer is NULL");
+    if (P > 0 && !r->self_pairs) return fail(ctx, VP_ERR_ARG, "self_pairs is NULL");
+    const int L = D + 1;
+
+    RobotParams rp;
+    std::memset(&rp, 0, sizeof(rp));
+    rp.n_joints = D;
+    rp.n_links = L;
+    rp.n_spheres = S;
+    rp.n_pairs = P;
+
+    // joints
+    std::vector<int> parent_link(D);
+    for (int j = 0; j < D; ++j) {
+        const int p = r->joint_parent[j];
+        if (p < -1 || p >= j) return fail(ctx, VP_ERR_ARG, "joint %d: parent %d must be -1 or an earlier joint", j, p);
+        parent_link[j] = p + 1;
+        const int t = r->joint_type[j];
+        if (t != VP_JOINT_REVOLUTE && t != VP_JOINT_PRISMATIC) return fail(ctx, VP_ERR_ARG, "joint %d: bad type %d", j, t);
+        const double *ax = r->joint_axis + 3 * j;
+        const double *o = r->joint_origin + 12 * j;
+        if (!finite_all(ax, 3) || !finite_all(o, 12)) return fail(ctx, VP_ERR_ARG, "joint %d: non-finite axis or origin", j);
+        const double n = norm3(ax);
+        if (std::fabs(n - 1.0) > 1e-6) return fail(ctx, VP_ERR_ARG, "joint %d: axis is not a unit vector", j);
+        JointC &J = rp.joints[j];
+        for (int i = 0; i < 12; ++i) J.o[i] = static_cast<float>(o[i]);
+        for (int i = 0; i < 3; ++i) J.ax[i] = static_cast<float>(ax[i] / n);
+        int meta = (t == VP_JOINT_PRISMATIC) ? kMetaPrismatic : 0;
+        bool rot_id = true;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) rot_id &= o[4 * a + b] == (a == b ? 1.0 : 0.0);
+        if (rot_id) meta |= kMetaOriginRotIdentity;
+        int axis = kAxisGeneral;
+        if (ax[0] == 1.0 && ax[1] == 0.0 && ax[2] == 0.0) axis = kAxisX;
+        if (ax[0] == 0.0 && ax[1] == 1.0 && ax[2] == 0.0) axis = kAxisY;
+        if (ax[0] == 0.0 && ax[1] == 0.0 && ax[2] == 1.0) axis = kAxisZ;
+        meta |= axis << kMetaAxisShift;
+        J.meta = meta;  // parent source filled in below
+    }
+
+    // spheres, sorted by link (stable)
+    std::vector<int> order(S);
+    for (int s = 0; s < S; ++s) {
+        const int l = r->sphere_link[s];
+        if (l < 0 || l >= L) return fail(ctx, VP_ERR_ARG, "sphere %d: link %d out of range", s, l);
+        if (!finite_all(r->sphere_centre + 3 * s, 3) || !std::isfinite(r->sphere_radius[s]) || r->sphere_radius[s] < 0)
+            return fail(ctx, VP_ERR_ARG, "sphere %d: bad centre or radius", s);
+        order[s] = s;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
+    std::vector<uint16_t> sorted_of(S);
+    for (int i = 0; i < S; ++i) {
+        const int s = order[i];
+        sorted_of[s] = static_cast<uint16_t>(i);
+        rp.perm[i] = static_cast<uint16_t>(s);
+        const double *c = r->sphere_centre + 3 * s;
+        rp.spheres[i] = float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
+                               static_cast<float>(r->sphere_radius[s])};
+    }
+    for (int l = 0; l < L; ++l) {
+        LinkC &K = rp.links[l];
+        K.slot = -1;
+        K.s0 = K.s1 = 0;
+        K.g0 = K.g1 = 0;
+        K.bs = float4{0.f, 0.f, 0.f, -1.f};
+    }
+    for (int i = 0; i < S;) {
+        const int l = r->sphere_link[order[i]];
+        int j = i;
+        while (j < S && r->sphere_link[order[j]] == l) ++j;
+        rp.links[l].s0 = static_cast<int16_t>(i);
+        rp.links[l].s1 = static_cast<int16_t>(j);
+        i = j;
+    }
+
+    // link bounding spheres (Sec. III-D mid-phase): given and checked, or derived
+    for (int l = 0; l < L; ++l) {
+        LinkC &K = rp.links[l];
+        if (K.s0 == K.s1) continue;
+        double c[3] = {0, 0, 0}, R = 0;
+        if (r->link_spheres) {
+            const double *g = r->link_spheres + 4 * l;
+            if (!finite_all(g, 4)) return fail(ctx, VP_ERR_ARG, "link sphere %d is not finite", l);
+            c[0] = g[0];
+            c[1] = g[1];
+            c[2] = g[2];
+            R = g[3];
+        } else {
+            for (int i = K.s0; i < K.s1; ++i)
+                for (int a = 0; a < 3; ++a) c[a] += r->sphere_centre[3 * order[i] + a];
+            for (int a = 0; a < 3; ++a) c[a] /= (K.s1 - K.s0);
+        }
+        double need = 0;
+        for (int i = K.s0; i < K.s1; ++i) {
+            const double *p = r->sphere_centre + 3 * order[i];
+            const double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+            need = std::max(need, norm3(d) + r->sphere_radius[order[i]]);
+        }
+        if (r->link_spheres) {
+            if (need > R + 1e-9)
+                return fail(ctx, VP_ERR_ARG, "link sphere %d does not contain its spheres (needs %.6g > %.6g)", l, need, R);
+        } else {
+            R = need;
+        }
+        K.bs = float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
+                      static_cast<float>(R) + kCoarseEps};
+    }
+
+    // self pairs grouped by (earlier link, later link), later link major
+    struct PairRec {
+        int la, lb, a, b;
+    };
+    std::vector<PairRec> prs(P);
+    for (int p = 0; p < P; ++p) {
+        int a = r->self_pairs[2 * p], b = r->self_pairs[2 * p + 1];
+        if (a < 0 || a >= S || b < 0 || b >= S || a == b)
+            return fail(ctx, VP_ERR_ARG, "self pair %d: bad sphere indices (%d, %d)", p, a, b);
+        int la = r->sphere_link[a], lb = r->sphere_link[b];
+        if (la > lb) {
+            std::swap(a, b);
+            std::swap(la, lb);
+        }
+        prs[p] = PairRec{la, lb, sorted_of[a], sorted_of[b]};
+    }
+    std::stable_sort(prs.begin(), prs.end(),
+                     [](const PairRec &x, const PairRec &y) { return x.lb != y.lb ? x.lb < y.lb : x.la < y.la; });
+    std::vector<int> slot_of(L, -1);
+    int n_slots = 0;
+    auto need_slot = [&](int l) {
+        if (l > 0 && slot_of[l] < 0) slot_of[l] = n_slots++;
+    };
+    int ng = 0;
+    for (int i = 0; i < P;) {
+        int j = i;
+        while (j < P && prs[j].la == prs[i].la && prs[j].lb == prs[i].lb) ++j;
+        if (ng >= kMaxGroups) return fail(ctx, VP_ERR_CAPACITY, "too many link pairs with self pairs");
+        GroupC &G = rp.groups[ng++];
+        G.la = static_cast<int16_t>(prs[i].la);
+        G.p0 = static_cast<int16_t>(i);
+        G.p1 = static_cast<int16_t>(j);
+        if (prs[i].la != prs[i].lb) need_slot(prs[i].la);
+        i = j;
+    }
+    for (int p = 0; p < P; ++p) rp.pairs[p] = PairC{static_cast<uint16_t>(prs[p].a), static_cast<uint16_t>(prs[p].b)};
+    // branch points: a joint whose parent is not the previous joint reads its
+    // parent's frame from the stash
+    for (int j = 0; j < D; ++j)
+        if (parent_link[j] != j && parent_link[j] != 0) need_slot(parent_link[j]);
+    for (int l = 0; l < L; ++l) rp.links[l].slot = static_cast<int16_t>(slot_of[l]);
+    for (int g = 0; g < ng; ++g) {
+        GroupC &G = rp.groups[g];
+        const int lb = prs[G.p0].lb;
+        G.slot_a = static_cast<int16_t>(G.la == lb ? kSlotSameLink : (G.la == 0 ? kSlotBase : slot_of[G.la]));
+    }
+    for (int g = 0; g < ng;) {
+        const int lb = prs[rp.groups[g].p0].lb;
+        int h = g;
+        while (h < ng && prs[rp.groups[h].p0].lb == lb) ++h;
+        rp.links[lb].g0 = static_cast<int16_t>(g);
+        rp.links[lb].g1 = static_cast<int16_t>(h);
+        g = h;
+    }
+    for (int j = 0; j < D; ++j) {
+        const int pl = parent_link[j];
+        const int src = (pl == j) ? kParentPrev : (pl == 0 ? kParentBase : slot_of[pl]);
+        rp.joints[j].meta |= (src & 0xFF) << kMetaParentShift;
+    }
+    rp.n_groups = ng;
+    rp.n_slots = n_slots;
+
+    ctx->robot = rp;
+    ctx->sorted_of = sorted_of;
+    ctx->robot_loaded = true;
+    batched_invalidate(ctx->batched);
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// environment
+
+extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!e) return fail(ctx, VP_ERR_ARG, "environment descriptor is NULL");
+    const int ns = e->n_spheres, nc = e->n_capsules, nb = e->n_cuboids;
+    if (ns < 0 || nc < 0 || nb < 0) return fail(ctx, VP_ERR_ARG, "negative primitive count");
+    if ((ns && !e->spheres) || (nc && !e->capsules) || (nb && !e->cuboids))
+        return fail(ctx, VP_ERR_ARG, "primitive table pointer is NULL");
+    const size_t n4 = static_cast<size_t>(ns) + 2 * static_cast<size_t>(nc) + 4 * static_cast<size_t>(nb);
+    if (n4 * 16 > VP_MAX_ENV_BYTES)
+        return fail(ctx, VP_ERR_CAPACITY, "environment packs to %zu bytes > %d", n4 * 16, VP_MAX_ENV_BYTES);
+    std::vector<float4> h(n4);
+    size_t k = 0;
+    for (int i = 0; i < ns; ++i) {
+        const double *p = e->spheres + 4 * i;
+        if (!finite_all(p, 4) || p[3] < 0) return fail(ctx, VP_ERR_ARG, "sphere %d is malformed", i);
+        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[3])};
+    }
+    for (int i = 0; i < nc; ++i) {
+        const double *p = e->capsules + 7 * i;
+        if (!finite_all(p, 7) || p[6] < 0) return fail(ctx, VP_ERR_ARG, "capsule %d is malformed", i);
+        const double u[3] = {p[3] - p[0], p[4] - p[1], p[5] - p[2]};
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[6])};
+        h[k++] = float4{float(u[0]), float(u[1]), float(u[2]), uu > 0 ? float(1.0 / uu) : 0.f};
+    }
+    for (int i = 0; i < nb; ++i) {
+        const double *p = e->cuboids + 15 * i;
+        if (!finite_all(p, 15) || p[12] < 0 || p[13] < 0 || p[14] < 0)
+            return fail(ctx, VP_ERR_ARG, "cuboid %d is malformed", i);
+        const double *c = p, *R = p + 3;
+        for (int a = 0; a < 3; ++a) {
+            // box axis a = column a of R
+            const double ax[3] = {R[0 * 3 + a], R[1 * 3 + a], R[2 * 3 + a]};
+            const double off = ax[0] * c[0] + ax[1] * c[1] + ax[2] * c[2];
+            h[k++] = float4{float(ax[0]), float(ax[1]), float(ax[2]), float(-off)};
+        }
+        h[k++] = float4{float(p[12]), float(p[13]), float(p[14]), 0.f};
+    }
+    DeviceGuard g(ctx->device);
+    float4 *buf = nullptr;
+    if (n4 > 0) {
+        cudaError_t err = cudaMalloc(&buf, n4 * 16);
+        if (err == cudaSuccess) err = cudaMemcpy(buf, h.data(), n4 * 16, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) {
+            if (buf) cudaFree(buf);
+            return cuda_fail(ctx, err, "vp_load_env");
+        }
+    }
+    if (ctx->env_buf) {
+        cudaDeviceSynchronize();  // the old buffer may still be read by queued work
+        cudaFree(ctx->env_buf);
+    }
+    ctx->env_buf = buf;
+    ctx->env = EnvView{buf, ns, nc, nb, static_cast<int>(n4)};
+    ctx->env_loaded = true;
+    batched_invalidate(ctx->batched);
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// compute calls
+
+namespace {
+
+// Largest block (128, 64 or 32 threads) whose shared memory fits the
+// opt-in limit; returns false if none does.
+bool plan_block(vp_ctx *ctx, int n_slots, int *block, size_t *smem) {
+    for (int b : {128, 64, 32}) {
+        const size_t s = smem_bytes(ctx->env, n_slots, b);
+        if (s <= ctx->smem_optin) {
+            *block = b;
+            *smem = s;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float *centres, void *stream) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "robot not loaded");
+    if (n < 0) return fail(ctx, VP_ERR_ARG, "n < 0");
+    if (n == 0) return VP_OK;
+    if (!q || !centres) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    const int block = 128;
+    const size_t smem = static_cast<size_t>(ctx->robot.n_slots) * kStashFloats * block * sizeof(float);
+    int bps = 0;
+    cudaError_t e = prepare_fk(smem, block, &bps);
+    if (e == cudaSuccess) {
+        const int64_t grid = (n + block - 1) / block;
+        e = launch_fk(ctx->robot, q, n, centres, static_cast<int>(grid), block, smem,
+                      static_cast<cudaStream_t>(stream));
+    }
+    return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_fk_spheres");
+}
+
+extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, uint8_t *valid, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (n < 0) return fail(ctx, VP_ERR_ARG, "n < 0");
+    if (n == 0) return VP_OK;
+    if (!q || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    int block = 0;
+    size_t smem = 0;
+    if (!plan_block(ctx, ctx->robot.n_slots, &block, &smem))
+        return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
+    int bps = 0;
+    cudaError_t e = prepare_states(smem, block, &bps);
+    if (e == cudaSuccess) {
+        const int64_t need = (n + block - 1) / block;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
+        e = launch_states(ctx->robot, ctx->env, q, n, valid, ctx->status, static_cast<int>(grid), block, smem,
+                          static_cast<cudaStream_t>(stream));
+    }
+    return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_states");
+}
+
+extern "C" vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float resolution,
+                                    int64_t n_edges, int32_t *counts, void *stream) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "robot not loaded");
+    if (n_edges < 0) return fail(ctx, VP_ERR_ARG, "n_edges < 0");
+    if (!(resolution > 0.f) || !std::isfinite(resolution)) return fail(ctx, VP_ERR_ARG, "resolution must be > 0");
+    if (n_edges == 0) return VP_OK;
+    if (!q0 || !q1 || !counts) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_counts(ctx->robot.n_joints, q0, q1, resolution, n_edges, counts,
+                                  static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_edge_counts");
+}
+
+static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                     float resolution, int64_t n_edges, uint8_t *valid, int mode,
+                                     uint64_t *work, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (n_edges < 0) return fail(ctx, VP_ERR_ARG, "n_edges < 0");
+    if (!counts && (!(resolution > 0.f) || !std::isfinite(resolution)))
+        return fail(ctx, VP_ERR_ARG, "resolution must be > 0 when counts is NULL");
+    if (mode != VP_MODE_PLAIN && mode != VP_MODE_BATCHED && mode != VP_MODE_PER_EDGE)
+        return fail(ctx, VP_ERR_ARG, "unknown mode %d", mode);
+    if (n_edges == 0) return VP_OK;
+    if (!q0 || !q1 || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (mode == VP_MODE_BATCHED && !work) {
+        BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
+                      ctx->num_sms, ctx->smem_optin, st};
+        std::string msg;
+        const int rc = batched_validate(ctx->batched, a, &msg);
+        if (rc == 0) return VP_OK;
+        return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "batched: %s", msg.c_str());
+    }
+    int block = 0;
+    size_t smem = 0;
+    if (!plan_block(ctx, ctx->robot.n_slots, &block, &smem))
+        return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
+    int bps = 0;
+    cudaError_t e = prepare_edges_plain(work != nullptr, smem, block, &bps);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges (prepare)");
+    if (bps < 1) return fail(ctx, VP_ERR_CAPACITY, "plain edge kernel cannot be resident");
+    const int wpb = block / 32;
+    if (mode == VP_MODE_PER_EDGE && !work) {
+        const int D = ctx->robot.n_joints;
+        for (int64_t i = 0; i < n_edges && e == cudaSuccess; ++i)
+            e = launch_edges_plain(ctx->robot, ctx->env, q0 + i * D, q1 + i * D, counts ? counts + i : nullptr,
+                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_slots, 32), st);
+        return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges (per edge)");
+    }
+    const int64_t need = (n_edges + wpb - 1) / wpb;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
+    e = launch_edges_plain(ctx->robot, ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
+                           reinterpret_cast<unsigned long long *>(work), static_cast<int>(grid), block, smem, st);
+    return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges");
+}
+
+extern "C" vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                       float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream) {
+    return validate_edges_impl(ctx, q0, q1, counts, resolution, n_edges, valid, mode, nullptr, stream);
+}
+
+extern "C" vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                            float resolution, int64_t n_edges, uint8_t *valid, uint64_t *work,
+                                            void *stream) {
+    if (ctx && !work) return fail(ctx, VP_ERR_ARG, "work is NULL");
+    return validate_edges_impl(ctx, q0, q1, counts, resolution, n_edges, valid, VP_MODE_PLAIN, work, stream);
+}
+
+extern "C" vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin, float *cost,
+                                       float *grad, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (n < 0) return fail(ctx, VP_ERR_ARG, "n < 0");
+    if (!std::isfinite(margin)) return fail(ctx, VP_ERR_ARG, "margin must be finite");
+    if (n == 0) return VP_OK;
+    if (!q || !cost) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    std::string msg;
+    const int rc = cost_launch(ctx->robot, ctx->env, q, n, margin, cost, grad, ctx->status, ctx->num_sms,
+                               ctx->smem_optin, static_cast<cudaStream_t>(stream), &msg);
+    if (rc == 0) return VP_OK;
+    return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_collision_cost: %s", msg.c_str());
+}
+
+extern "C" vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                 float resolution, int64_t n_edges, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (n_edges <= 0) return fail(ctx, VP_ERR_ARG, "n_edges must be > 0");
+    if (!q0 || !q1) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    if (!counts && (!(resolution > 0.f) || !std::isfinite(resolution)))
+        return fail(ctx, VP_ERR_ARG, "resolution must be > 0 when counts is NULL");
+    DeviceGuard g(ctx->device);
+    BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, nullptr, ctx->status,
+                  ctx->num_sms, ctx->smem_optin, static_cast<cudaStream_t>(stream)};
+    std::string msg;
+    const int rc = batched_autotune(ctx->batched, a, &msg);
+    if (rc == 0) return VP_OK;
+    return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_autotune: %s", msg.c_str());
+}
+
+extern "C" vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits) {
+    if (!ctx) return VP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_sync_status");
+    if (bits) *bits = h;
+    if (h & VP_DEVERR_TIMEOUT) return fail(ctx, VP_ERR_TIMEOUT, "device watchdog fired (status 0x%x)", h);
+    if (h) return fail(ctx, VP_ERR_DEVICE, "device reported bad input (status 0x%x)", h);
+    return VP_OK;
+}

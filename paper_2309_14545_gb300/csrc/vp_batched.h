@@ -1,0 +1,37 @@
+// Batched edge validation: persistent, length-bucketed work queue with a
+// tuned tiling, replayed from a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "vp_types.h"
+
+namespace vp {
+
+struct BatchedArgs {
+    const RobotParams *robot;
+    const EnvView *env;
+    const float *q0, *q1;
+    const int32_t *counts;
+    float res;
+    int64_t E;
+    uint8_t *valid;
+    unsigned *status;
+    int num_sms;
+    size_t smem_optin;
+    cudaStream_t stream;
+};
+
+struct BatchedState {
+    void *impl = nullptr;
+};
+
+// 0 = ok, 1 = capacity, 2 = CUDA error (message in *msg)
+int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg);
+int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg);
+void batched_invalidate(BatchedState &st);
+void batched_release(BatchedState &st);
+
+}  // namespace vp

@@ -1,0 +1,276 @@
+// Kernels of the plain path: edge validation (one warp per edge, raked
+// states), state validation, FK sphere centres and edge state counts.
+#include <cuda_runtime.h>
+
+#include "vp_device.cuh"
+#include "vp_internal.h"
+
+namespace vp {
+
+size_t smem_bytes(const EnvView &env, int n_slots, int block) {
+    const size_t warps = static_cast<size_t>((block + 31) / 32);
+    return static_cast<size_t>(env.n_float4) * 16 + 16 + warps * 32 * sizeof(float) +
+           static_cast<size_t>(n_slots) * kStashFloats * block * sizeof(float);
+}
+
+// State count of an edge from its largest joint displacement (float32, IEEE
+// division): max(2, ceil(dmax / res) + 1); -1 past VP_MAX_STEPS.
+__device__ __forceinline__ int count_from_dmax(float dmax, float res) {
+    const float steps = ceilf(__fdiv_rn(dmax, res));
+    if (!(steps <= static_cast<float>(VP_MAX_STEPS))) return -1;
+    return max(2, static_cast<int>(steps) + 1);
+}
+
+struct SmemCarve {
+    float4 *env;
+    uint64_t *bar;
+    float *warp_buf;
+    float *stash;
+};
+
+__device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &env) {
+    SmemCarve c;
+    size_t off = static_cast<size_t>(env.n_float4) * 16;
+    c.env = reinterpret_cast<float4 *>(smem);
+    c.bar = reinterpret_cast<uint64_t *>(smem + off);
+    off += 16;
+    c.warp_buf = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>((blockDim.x + 31) / 32) * 32 * sizeof(float);
+    c.stash = reinterpret_cast<float *>(smem + off);
+    return c;
+}
+
+__device__ __forceinline__ EnvSm env_view(const float4 *sm, const EnvView &env) {
+    EnvSm e;
+    e.sph = sm;
+    e.cap = sm + env.ns;
+    e.box = sm + env.ns + 2 * env.nc;
+    e.ns = env.ns;
+    e.nc = env.nc;
+    e.nb = env.nb;
+    return e;
+}
+
+template <bool STATS>
+__device__ __forceinline__ void flush_work(Work &wk, unsigned long long *work, int lane) {
+    if constexpr (STATS) {
+#pragma unroll
+        for (int i = 0; i < VP_WORK_N; ++i) {
+            const unsigned s = __reduce_add_sync(kFull, wk.v[i]);
+            if (lane == 0 && s) atomicAdd(work + i, static_cast<unsigned long long>(s));
+            wk.v[i] = 0;
+        }
+    }
+}
+
+// One warp per edge.  Lane j of the warp checks states j*R + r in round r
+// (R = ceil(k/32) rounds): the rake of Sec. III-D, 32 spread states per
+// round.  Lanes past the end park on the last state.
+template <bool STATS>
+__global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+                                                          const float *__restrict__ q0, const float *__restrict__ q1,
+                                                          const int32_t *__restrict__ counts, const float res,
+                                                          const long long E, uint8_t *__restrict__ valid,
+                                                          unsigned *status, unsigned long long *work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemCarve sc = carve(smem, env);
+    if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
+    const EnvSm es = env_view(sc.env, env);
+    const Stash stash{sc.stash, static_cast<int>(blockDim.x)};
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    float *wq0 = sc.warp_buf + wib * 32;
+    float *wdq = wq0 + 16;
+    const int D = P.n_joints;
+    Work wk;
+    if (STATS) {
+#pragma unroll
+        for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
+    }
+    for (long long e = static_cast<long long>(blockIdx.x) * wpb + wib; e < E;
+         e += static_cast<long long>(gridDim.x) * wpb) {
+        float a = 0.f, b = 0.f;
+        if (lane < D) {
+            a = q0[e * D + lane];
+            b = q1[e * D + lane];
+        }
+        const bool fin = isfinite(a) && isfinite(b);
+        const float d = b - a;
+        const bool all_fin = __all_sync(kFull, fin);
+        const float dmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(fin ? fabsf(d) : 0.f)));
+        if (lane < 16) {
+            wq0[lane] = a;
+            wdq[lane] = d;
+        }
+        __syncwarp();
+        int k = 2;
+        bool ok = all_fin;
+        if (counts != nullptr) {
+            k = counts[e];
+            if (k < 2) {
+                ok = false;
+                if (lane == 0) atomicOr(status, VP_DEVERR_COUNT);
+            }
+        } else if (ok) {
+            k = count_from_dmax(dmax, res);
+            if (k < 0) {
+                ok = false;
+                if (lane == 0) atomicOr(status, VP_DEVERR_LENGTH);
+            }
+        }
+        bool collided = !ok;
+        if (ok) {
+            const int R = (k + 31) >> 5;
+            const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
+            for (int r = 0; r < R; ++r) {
+                int i = lane * R + r;
+                const bool real = i < k;
+                if (!real) i = k - 1;
+                const float t = static_cast<float>(i) * inv;
+                const WorkRef<STATS> w{&wk, real};
+                const bool c = pose_and_check<true, STATS>(
+                    P, [&](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, kFull, w);
+                if (__any_sync(kFull, c)) {
+                    collided = true;
+                    break;
+                }
+            }
+        }
+        if (lane == 0) valid[e] = collided ? 0 : 1;
+        if (STATS) {
+            wk.v[VP_WORK_EDGES_DONE] += (lane == 0);
+            flush_work<STATS>(wk, work, lane);
+        }
+        __syncwarp();
+    }
+}
+
+// One lane per configuration; lanes are independent (a warp stops once all
+// its lanes collided).
+__global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+                                                     const float *__restrict__ q, const long long N,
+                                                     uint8_t *__restrict__ valid, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemCarve sc = carve(smem, env);
+    if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
+    const EnvSm es = env_view(sc.env, env);
+    const Stash stash{sc.stash, static_cast<int>(blockDim.x)};
+    const int lane = threadIdx.x & 31;
+    const int D = P.n_joints;
+    const long long step = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < N;
+         base += step) {
+        long long i = base + lane;
+        const bool real = i < N;
+        if (!real) i = N - 1;
+        const float *qi = q + i * D;
+        bool fin = true;
+        for (int j = 0; j < D; ++j) fin &= isfinite(qi[j]);
+        const WorkRef<false> w{nullptr, false};
+        const bool c = pose_and_check<false, false>(P, [&](int j) { return qi[j]; }, es, stash, kFull, w);
+        if (real) valid[i] = (c || !fin) ? 0 : 1;
+    }
+}
+
+// FK sphere centres: one thread per configuration.
+__global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
+                                                 const long long N, float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Stash stash{reinterpret_cast<float *>(smem), static_cast<int>(blockDim.x)};
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int D = P.n_joints, S = P.n_spheres;
+    const float *qi = q + i * D;
+    float *oi = out + i * 3 * S;
+    Fr f;
+    fr_identity(f);
+    for (int l = 0; l <= D; ++l) {
+        if (l > 0) {
+            const JointC &J = P.joints[l - 1];
+            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+            if (pm == kParentBase)
+                fr_identity(f);
+            else if (pm != kParentPrev)
+                stash.load(pm, f);
+            apply_joint(J, qi[l - 1], f);
+            if (P.links[l].slot >= 0) stash.store(P.links[l].slot, f, make_float3(0.f, 0.f, 0.f));
+        }
+        const LinkC &L = P.links[l];
+        for (int s = L.s0; s < L.s1; ++s) {
+            const float4 sp = P.spheres[s];
+            const float3 c = fr_apply(f, sp.x, sp.y, sp.z);
+            float *o = oi + 3 * P.perm[s];
+            o[0] = c.x;
+            o[1] = c.y;
+            o[2] = c.z;
+        }
+    }
+}
+
+__global__ void counts_kernel(const int D, const float *__restrict__ q0, const float *__restrict__ q1,
+                              const float res, const long long E, int32_t *__restrict__ counts) {
+    const long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    float dmax = 0.f;
+    bool fin = true;
+    for (int j = 0; j < D; ++j) {
+        const float a = q0[e * D + j], b = q1[e * D + j];
+        fin &= isfinite(a) && isfinite(b);
+        if (fin) dmax = fmaxf(dmax, fabsf(b - a));
+    }
+    counts[e] = fin ? count_from_dmax(dmax, res) : -1;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+template <class K>
+static cudaError_t prepare(K kernel, size_t smem, int block, int *blocks_per_sm) {
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
+}
+
+cudaError_t prepare_edges_plain(bool stats, size_t smem, int block, int *blocks_per_sm) {
+    return stats ? prepare(edges_plain_kernel<true>, smem, block, blocks_per_sm)
+                 : prepare(edges_plain_kernel<false>, smem, block, blocks_per_sm);
+}
+
+cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
+                               const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
+                               unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st) {
+    if (work)
+        edges_plain_kernel<true><<<grid, block, smem, st>>>(P, env, q0, q1, counts, res, E, valid, status, work);
+    else
+        edges_plain_kernel<false><<<grid, block, smem, st>>>(P, env, q0, q1, counts, res, E, valid, status, work);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_states(size_t smem, int block, int *blocks_per_sm) {
+    return prepare(states_kernel, smem, block, blocks_per_sm);
+}
+
+cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
+                          unsigned *status, int grid, int block, size_t smem, cudaStream_t st) {
+    states_kernel<<<grid, block, smem, st>>>(P, env, q, N, valid, status);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_fk(size_t smem, int block, int *blocks_per_sm) {
+    return prepare(fk_kernel, smem, block, blocks_per_sm);
+}
+
+cudaError_t launch_fk(const RobotParams &P, const float *q, int64_t N, float *centres, int grid, int block,
+                      size_t smem, cudaStream_t st) {
+    fk_kernel<<<grid, block, smem, st>>>(P, q, N, centres);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts(int D, const float *q0, const float *q1, float res, int64_t E, int32_t *counts,
+                          cudaStream_t st) {
+    const int block = 256;
+    const long long grid = (E + block - 1) / block;
+    counts_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(D, q0, q1, res, E, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace vp

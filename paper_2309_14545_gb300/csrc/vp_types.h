@@ -1,0 +1,89 @@
+// Packed robot and environment tables shared by the host packer and the
+// kernels.  The robot travels as a __grid_constant__ kernel parameter (it
+// lives in the constant bank, read with warp-uniform indices); the
+// environment is a float4 buffer that every block stages into shared memory.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/vp.h"
+
+#ifndef __CUDACC__
+struct alignas(16) float4 { float x, y, z, w; };
+#endif
+
+namespace vp {
+
+constexpr int kMaxJoints = VP_MAX_JOINTS;
+constexpr int kMaxLinks = VP_MAX_JOINTS + 1;
+constexpr int kMaxSpheres = VP_MAX_SPHERES;
+constexpr int kMaxPairs = VP_MAX_PAIRS;
+constexpr int kMaxGroups = 160;  // link pairs holding self pairs (<= 17*18/2)
+
+// JointC::meta bit fields
+constexpr int kMetaPrismatic = 1 << 0;
+constexpr int kMetaOriginRotIdentity = 1 << 1;
+constexpr int kMetaAxisShift = 2;  // 2 bits: 0 x, 1 y, 2 z, 3 general
+constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2, kAxisGeneral = 3;
+constexpr int kMetaParentShift = 8;  // 8 bits: parent frame source
+constexpr int kParentPrev = 0xFF;    // the previous joint's link (kept in registers)
+constexpr int kParentBase = 0xFE;    // the base (identity)
+// any other value: the stash slot holding the parent link's frame
+
+// GroupC::slot_a special values
+constexpr int kSlotSameLink = -1;  // both spheres on the current link
+constexpr int kSlotBase = -2;      // earlier link is the base (identity frame)
+
+// Floats kept per stash slot: frame [R row-major | p] (12) + world centre of
+// the link's bounding sphere (3).
+constexpr int kStashFloats = 15;
+
+// Conservative inflation of every link bounding sphere (m): covers float32
+// rounding in the coarse test so a coarse miss never hides a fine hit.
+constexpr float kCoarseEps = 1e-5f;
+
+struct JointC {  // 64 bytes
+    float o[12];  // fixed origin [R | t], row-major
+    float ax[3];  // unit axis in the joint frame
+    int meta;
+};
+
+struct LinkC {  // 32 bytes
+    float4 bs;      // bounding sphere: centre (link frame), radius (+eps); radius < 0: no spheres
+    int16_t s0, s1;  // fine spheres [s0, s1) in sorted order
+    int16_t g0, g1;  // self groups [g0, g1) checked once this link is posed
+    int16_t slot;    // stash slot for this link's frame, -1 if none
+    int16_t pad[3];
+};
+
+struct GroupC {      // one link pair (la < lb) and its sphere pairs
+    int16_t la;      // earlier link
+    int16_t slot_a;  // stash slot of la, or kSlotSameLink / kSlotBase
+    int16_t p0, p1;  // pairs [p0, p1)
+};
+
+struct PairC {
+    uint16_t a, b;  // sorted sphere indices: a on the group's la, b on lb
+};
+
+struct RobotParams {
+    int n_joints, n_links, n_spheres, n_pairs, n_groups, n_slots;
+    int pad0, pad1;
+    JointC joints[kMaxJoints];
+    LinkC links[kMaxLinks];
+    float4 spheres[kMaxSpheres];  // local centre, radius (sorted by link)
+    GroupC groups[kMaxGroups];
+    PairC pairs[kMaxPairs];
+    uint16_t perm[kMaxSpheres];   // sorted index -> caller's sphere index
+};
+
+// Environment layout (float4 units): spheres [ns] (c, r); capsules [2 nc]
+// ((p0, r), (u = p1 - p0, 1/|u|^2)); cuboids [4 nb] ((a_i, -a_i . c) for the
+// three box axes a_i, then (h, 0)).
+struct EnvView {
+    const float4 *data;
+    int ns, nc, nb;
+    int n_float4;  // total float4 count
+};
+
+}  // namespace vp

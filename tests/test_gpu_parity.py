@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (from the method's numerics): sphere centres within 1e-5 m; state and
+edge verdicts bit-exact wherever the oracle's clearance is outside the
+1e-4 m band (band states / edges are counted, not compared); state counts
+and every integer output bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import vpgen
+
+pytestmark = pytest.mark.gpu
+
+CENTRE_TOL = 1e-5
+BAND = oracle.BAND
+
+
+@pytest.fixture(scope="module")
+def vpmod(cuda_ok):
+    from paper_2309_14545_gb300 import build
+    build.build()
+    from paper_2309_14545_gb300 import Validator, vp
+    return Validator, vp
+
+
+_cache = {}
+
+
+def _setup(vpmod, cfg, n_edges):
+    key = (cfg, n_edges)
+    if key not in _cache:
+        Validator, _ = vpmod
+        w = vpgen.workload(cfg, n_edges=n_edges)
+        _cache[key] = (w, Validator(w.robot, w.env), oracle.Oracle(w.robot, w.env))
+    return _cache[key]
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2])
+def test_fk_centres(vpmod, cfg):
+    w, val, o = _setup(vpmod, cfg, 64)
+    q = vpgen.uniform_configs(w.robot, 4099, seed=31)  # ragged: not a multiple of the block
+    got = val.fk_spheres(_cuda(q)).cpu().numpy()
+    want = o.fk(q.astype(np.float64))
+    err = np.abs(got - want).max()
+    assert err <= CENTRE_TOL, err
+
+
+def test_fk_general_tree_and_axes(vpmod):
+    """A branching tree with general origin rotations and axes exercises the
+    frame stash and the Rodrigues path."""
+    from robots_small import EMPTY_ENV, random_chain
+    Validator, _ = vpmod
+    rng = np.random.default_rng(5)
+    r = random_chain(rng, D=9, n_spheres=40)
+    r.joint_parent = np.array([-1, 0, 1, 2, 1, 4, -1, 6, 3], dtype=np.int32)
+    val = Validator(r, EMPTY_ENV)
+    q = rng.uniform(-2, 2, size=(1000, 9)).astype(np.float32)
+    got = val.fk_spheres(_cuda(q)).cpu().numpy()
+    want = oracle.Oracle(r, EMPTY_ENV).fk(q.astype(np.float64))
+    assert np.abs(got - want).max() <= CENTRE_TOL
+
+
+def test_edge_counts_bit_exact(vpmod):
+    w, val, o = _setup(vpmod, 0, 4096)
+    got = val.edge_counts(_cuda(w.q0), _cuda(w.q1), w.res).cpu().numpy()
+    assert np.array_equal(got, o.edge_count(w.q0, w.q1, w.res))
+    # hand cases incl. the float32 decision, non-finite and over-long edges
+    q0 = np.zeros((6, 7), np.float32)
+    q1 = np.zeros((6, 7), np.float32)
+    q0[1, 0], q1[1, 0] = np.float32(-1e-8), 1.0
+    q1[2, 3] = np.nextafter(np.float32(1 / 32), np.float32(1))
+    q0[3, 2] = np.nan
+    q1[4, 6] = np.inf
+    q1[5, 1] = 1e7
+    got = val.edge_counts(_cuda(q0), _cuda(q1), w.res).cpu().numpy()
+    assert list(got) == [2, 33, 3, -1, -1, -1]
+    assert np.array_equal(got, o.edge_count(q0, q1, w.res))
+
+
+def _compare_states(val, o, q):
+    got = val.validate_states(_cuda(q)).cpu().numpy()
+    K = o.clearance(q.astype(np.float64))
+    pinned = np.abs(K) > BAND
+    bad = np.nonzero(got[pinned] != (K[pinned] >= 0))[0]
+    return got, K, pinned, bad
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
+def test_state_verdicts(vpmod, cfg):
+    w, val, o = _setup(vpmod, cfg, 64)
+    q = vpgen.uniform_configs(w.robot, 3001 if cfg != 4 else 1001, seed=41 + cfg)
+    got, K, pinned, bad = _compare_states(val, o, q)
+    assert bad.size == 0, f"{bad.size} pinned states disagree"
+    assert pinned.mean() > 0.99
+    assert 0 < got.mean() < 1 or cfg == 4
+
+
+def _compare_edges(w, val, o, idx, mode, n_edges=None):
+    from paper_2309_14545_gb300 import vp
+    q0, q1 = _cuda(w.q0), _cuda(w.q1)
+    counts = None if w.counts is None else _cuda(w.counts)
+    got = val.validate_edges(q0, q1, counts, float(w.res), mode=mode).cpu().numpy()
+    st, bits = val.sync_status()
+    assert st == vp.VP_OK, (st, bits)
+    c = None if w.counts is None else w.counts[idx]
+    cls, nb = o.classify_edges(w.q0[idx], w.q1[idx], c, w.res)
+    pinned = cls != 2
+    bad = np.nonzero(got[idx][pinned] != (cls[pinned] == 0))[0]
+    return got, cls, bad
+
+
+def test_edges_config0_every_edge(vpmod):
+    """Config 0 at full size (10,000 edges): every pinned edge matches."""
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, 0, None)
+    idx = np.arange(w.q0.shape[0])
+    got, cls, bad = _compare_edges(w, val, o, idx, vp.VP_MODE_PLAIN)
+    assert bad.size == 0, f"{bad.size} pinned edges disagree"
+    assert (cls == 2).mean() < 0.01
+    assert 0.2 < got.mean() < 0.9
+
+
+@pytest.mark.parametrize("cfg,n_sample", [(1, 768), (2, 512), (4, 256)])
+def test_edges_full_size_sampled(vpmod, cfg, n_sample):
+    """Full-size workloads in the benchmark's launch configuration, checked
+    on a seeded sample of edges the oracle classifies one by one."""
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, cfg, None)
+    idx = np.sort(np.random.default_rng(cfg).choice(w.q0.shape[0], n_sample, replace=False))
+    got, cls, bad = _compare_edges(w, val, o, idx, vp.VP_MODE_PLAIN)
+    assert bad.size == 0, f"{bad.size} pinned edges disagree"
+
+
+def test_edge_edge_cases(vpmod):
+    """Empty input, a single edge, two-state and constant edges, explicit
+    maximum counts, non-finite endpoints and a count < 2 (reported through
+    the device status word, edge invalid)."""
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, 0, 2000)
+    empty = torch.zeros((0, 7), dtype=torch.float32, device="cuda")
+    out = val.validate_edges(empty, empty, None, float(w.res))
+    assert out.numel() == 0
+    n = 37  # ragged
+    q0 = w.q0[:n].copy()
+    q1 = w.q1[:n].copy()
+    counts = np.full(n, 2, np.int32)
+    counts[5:10] = 512
+    q1[10:15] = q0[10:15]           # constant edges
+    q0[15, 3] = np.nan              # non-finite endpoint
+    q1[16, 0] = np.inf
+    got = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), float(w.res)).cpu().numpy()
+    st, bits = val.sync_status()
+    assert st == vp.VP_OK
+    cls, _ = o.classify_edges(q0, q1, counts, w.res)
+    pinned = cls != 2
+    assert np.array_equal(got[pinned], (cls[pinned] == 0).astype(np.uint8))
+    assert got[15] == 0 and got[16] == 0
+    counts[3] = 1
+    got = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), float(w.res)).cpu().numpy()
+    st, bits = val.sync_status()
+    assert st == vp.VP_ERR_DEVICE and bits & vp.VP_DEVERR_COUNT
+    assert got[3] == 0
+    assert val.sync_status()[0] == vp.VP_OK  # cleared
+
+
+def test_per_edge_launches_match_plain(vpmod):
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, 2, 300)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    a = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    b = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PER_EDGE).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_work_counters(vpmod):
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, 1, 4096)
+    q0, q1 = _cuda(w.q0), _cuda(w.q1)
+    a = val.validate_edges(q0, q1, None, float(w.res)).cpu().numpy()
+    b, work = val.validate_edges_work(q0, q1, None, float(w.res))
+    work = work.cpu().numpy()
+    assert np.array_equal(a, b.cpu().numpy())
+    assert work[vp.VP_WORK_EDGES_DONE] == 4096
+    assert work[vp.VP_WORK_STATES] >= 4096
+    # every posed state runs the coarse test of each sphere-carrying link
+    # against every primitive until it stops
+    assert work[vp.VP_WORK_COARSE_CUBOID] > 0 and work[vp.VP_WORK_COARSE_SPHERE] == 0
+
+
+def test_argument_errors(vpmod):
+    Validator, vp = vpmod
+    w, val, o = _setup(vpmod, 0, 64)
+    bad = vpgen.arm7(0, 40)
+    bad.joint_parent = np.array([-1, 0, 5, 2, 3, 4, 5], dtype=np.int32)  # parent after child
+    with pytest.raises(vp.VPError) as e:
+        vp.vp_load_robot(val.ctx, bad)
+    assert e.value.status == vp.VP_ERR_ARG
+    big = vpgen.Env(np.zeros((20000, 4)) + [0, 0, 0, 0.1], np.zeros((0, 7)), np.zeros((0, 15)))
+    with pytest.raises(vp.VPError) as e:
+        vp.vp_load_env(val.ctx, big)
+    assert e.value.status == vp.VP_ERR_CAPACITY
+    q = torch.zeros((4, 7), device="cuda")
+    with pytest.raises(vp.VPError) as e:
+        val.validate_edges(q, q, None, 0.0)
+    assert e.value.status == vp.VP_ERR_ARG
