@@ -7,5 +7,18 @@ pairs, and early exit -- as hand-written CUDA kernels for sm_103a behind the
 C ABI in include/vp.h.  ``vp`` is the thin ctypes binding (same names as the
 C calls); ``Validator`` owns a context; ``CollisionCost`` wraps the
 penetration cost and its FK adjoint as a torch.autograd.Function.
+
+``build`` compiles libvp.so; everything else loads it on first use and
+raises if it is missing (there is no CPU fallback).
 """
-from .api import CollisionCost, Validator  # noqa: F401
+
+__all__ = ["Validator", "CollisionCost", "vp", "build"]
+
+
+def __getattr__(name):
+    import importlib
+    if name in ("Validator", "CollisionCost"):
+        return getattr(importlib.import_module(".api", __name__), name)
+    if name in ("vp", "build", "api"):
+        return importlib.import_module("." + name, __name__)
+    raise AttributeError(name)
