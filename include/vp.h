@@ -215,6 +215,48 @@ vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32
  * returned in *bits when bits != NULL. */
 vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits);
 
+/*
+ * Edge validation that allocates no device memory.
+ *
+ * The paper has no counterpart to this call.  It serves callers that must
+ * not allocate device memory while they run -- e.g. a planner re-validating
+ * edges inside a robot's real-time control loop, where cudaMalloc can block,
+ * synchronise the device and take unbounded time, or a process whose device
+ * memory is fixed at start-up.  Such callers cannot create a vp_ctx
+ * (vp_create and vp_load_env allocate), so this call takes the robot and
+ * environment descriptors directly and produces the same verdicts as
+ * vp_validate_edges in VP_MODE_PLAIN.
+ *
+ * Scratch: the packed environment and the device status word live in one
+ * file-scope static __device__ array of 256 + VP_NOALLOC_MAX_ENV_BYTES
+ * bytes, which every GPU that loads the library holds until the process
+ * exits.  An environment that packs to more than VP_NOALLOC_MAX_ENV_BYTES
+ * (sphere 16 B, capsule 32 B, cuboid 64 B each) is rejected with
+ * VP_ERR_CAPACITY before anything runs.  The call calls no cudaMalloc,
+ * cudaFree or other device-allocating routine; host side it packs the robot
+ * with small temporaries and stages the environment in a per-thread static
+ * buffer.
+ *
+ * Runs on the calling thread's current device.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and the
+ * device's launch limits; make that first call before any stream capture.
+ * Every call shares the array and it keeps the previous call's contents:
+ * each call restages the environment and clears the status word on
+ * `stream` first.  Calls that overlap on the GPU (other host threads, other
+ * streams) race on the array and must be serialised by the caller.
+ *
+ * Arguments are those of vp_validate_edges (q0, q1, counts, valid: device
+ * pointers on the current device; `stream`: a cudaStream_t or NULL).  The
+ * call returns after the work on `stream` has finished; device-side input
+ * errors come back as VP_ERR_DEVICE (the affected edges are reported
+ * invalid).  If errbuf != NULL, a message of at most errbuf_len bytes
+ * (NUL-terminated) describes a failure.
+ */
+#define VP_NOALLOC_MAX_ENV_BYTES (64 * 1024)
+vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const vp_env_desc *env, const float *q0,
+                                    const float *q1, const int32_t *counts, float resolution, int64_t n_edges,
+                                    uint8_t *valid, void *stream, char *errbuf, int32_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -557,3 +557,22 @@ extern "C" vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits) {
     if (h) return fail(ctx, VP_ERR_DEVICE, "device reported bad input (status 0x%x)", h);
     return VP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// robot packing without a context (used by the allocation-free entry point)
+
+namespace vp {
+
+// Packs `r` exactly as vp_load_robot does, through a context that owns no
+// device resources (vp_load_robot itself touches no device memory).
+vp_status pack_robot_host(const vp_robot_desc *r, RobotParams *out, std::string *err) {
+    vp_ctx host_only;
+    const vp_status s = vp_load_robot(&host_only, r);
+    if (s == VP_OK)
+        *out = host_only.robot;
+    else if (err)
+        *err = host_only.err;
+    return s;
+}
+
+}  // namespace vp

@@ -23,6 +23,7 @@ VP_MODE_PLAIN, VP_MODE_BATCHED, VP_MODE_PER_EDGE = 0, 1, 2
 VP_DEVERR_COUNT, VP_DEVERR_LENGTH, VP_DEVERR_TIMEOUT = 0x1, 0x2, 0x4
 VP_MAX_JOINTS, VP_MAX_SPHERES, VP_MAX_PAIRS = 16, 256, 1024
 VP_MAX_ENV_BYTES = 160 * 1024
+VP_NOALLOC_MAX_ENV_BYTES = 64 * 1024
 VP_MAX_STEPS = 16777216
 (VP_WORK_STATES, VP_WORK_LINK_CENTRES, VP_WORK_COARSE_SPHERE, VP_WORK_COARSE_CAPSULE, VP_WORK_COARSE_CUBOID,
  VP_WORK_FINE_SPHERE, VP_WORK_FINE_CAPSULE, VP_WORK_FINE_CUBOID, VP_WORK_PAIR_COARSE, VP_WORK_PAIR_FINE,
@@ -32,7 +33,7 @@ VP_WORK_N = 16
 #: Every symbol include/vp.h declares.
 EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load_env", "vp_fk_spheres",
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
-           "vp_collision_cost", "vp_autotune", "vp_sync_status")
+           "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc")
 
 
 class VPError(RuntimeError):
@@ -72,6 +73,7 @@ def _load_lib():
         "vp_collision_cost": (U, [P, P, I64, F, P, P, P]),
         "vp_autotune": (U, [P, P, P, P, F, I64, P]),
         "vp_sync_status": (U, [P, P, C.POINTER(C.c_uint32)]),
+        "vp_validate_edges_noalloc": (U, [P, P, P, P, P, F, I64, P, P, C.c_char_p, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,3 +222,36 @@ def vp_sync_status(ctx, stream=None):
     bits = C.c_uint32(0)
     st = lib.vp_sync_status(ctx, _stream(stream), C.byref(bits))
     return st, bits.value
+
+
+def vp_validate_edges_noalloc(robot, env, q0, q1, counts, resolution, valid, stream=None):
+    """Edge validation without a context and without device allocation (see
+    include/vp.h): the packed environment and the status word live in a
+    static device array of the library.  Synchronous on `stream`."""
+    E = q0.shape[0]
+    D = int(np.asarray(robot.joint_type).shape[0])
+    S = int(np.asarray(robot.sphere_radius).shape[0])
+    pairs = _arr(robot.self_pairs, np.int32, (-1, 2))
+    keep = [
+        _arr(robot.joint_parent, np.int32, (D,)), _arr(robot.joint_type, np.int32, (D,)),
+        _arr(robot.joint_axis, np.float64, (D, 3)), _arr(robot.joint_origin, np.float64, (D, 3, 4)),
+        _arr(robot.sphere_link, np.int32, (S,)), _arr(robot.sphere_centre, np.float64, (S, 3)),
+        _arr(robot.sphere_radius, np.float64, (S,)),
+        None if getattr(robot, "link_spheres", None) is None else _arr(robot.link_spheres, np.float64, (D + 1, 4)),
+        pairs,
+    ]
+    ptr = [None if a is None or a.size == 0 else a.ctypes.data for a in keep]
+    rdesc = vp_robot_desc(D, ptr[0], ptr[1], ptr[2], ptr[3], S, ptr[4], ptr[5], ptr[6], ptr[7],
+                          pairs.shape[0], ptr[8])
+    s = _arr(env.spheres, np.float64, (-1, 4))
+    c = _arr(env.capsules, np.float64, (-1, 7))
+    b = _arr(env.cuboids, np.float64, (-1, 15))
+    p = [a.ctypes.data if a.size else None for a in (s, c, b)]
+    edesc = vp_env_desc(s.shape[0], p[0], c.shape[0], p[1], b.shape[0], p[2])
+    buf = C.create_string_buffer(512)
+    st = lib.vp_validate_edges_noalloc(C.byref(rdesc), C.byref(edesc), _dev(q0, torch.float32, "q0"),
+                                       _dev(q1, torch.float32, "q1", q0.shape),
+                                       _dev(counts, torch.int32, "counts", (E,)), C.c_float(resolution), E,
+                                       _dev(valid, torch.uint8, "valid", (E,)), _stream(stream), buf, 512)
+    if st != VP_OK:
+        raise VPError(st, buf.value.decode())
