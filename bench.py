@@ -44,6 +44,8 @@ FLOPS_CENTRE = 18                 # R c + p (9 FMA)
 FLOPS_TEST = {"sphere": 10, "capsule": 22, "cuboid": 26}  # squared-distance ball tests
 FLOPS_PAIR_COARSE = 10            # link centres already posed
 FLOPS_PAIR_FINE = 2 * FLOPS_CENTRE + 10
+WORK_NAMES = ("states", "link_centres", "coarse_sphere", "coarse_capsule", "coarse_cuboid", "fine_sphere",
+              "fine_capsule", "fine_cuboid", "pair_coarse", "pair_fine", "edges")
 
 
 def _git_rev():
@@ -365,6 +367,7 @@ def run_native(args):
         "extra": {"mode": args.mode, "edges_per_s": edges_all / (t_max / 1000.0),
                   "evaluated_states_per_s": world * int(work[vp.VP_WORK_STATES]) / (t_max / 1000.0),
                   "covered_states_per_step": covered_all, "valid_edge_fraction": valid_frac,
+                  "work_per_step": {n: int(work[i]) for i, n in enumerate(WORK_NAMES)},
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
     if not args.no_cpu_baseline:

@@ -263,11 +263,11 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     }
     std::stable_sort(prs.begin(), prs.end(),
                      [](const PairRec &x, const PairRec &y) { return x.lb != y.lb ? x.lb < y.lb : x.la < y.la; });
-    std::vector<int> slot_of(L, -1);
-    int n_slots = 0;
-    auto need_slot = [&](int l) {
-        if (l > 0 && slot_of[l] < 0) slot_of[l] = n_slots++;
-    };
+    // stash slots: centre slots for links that are the earlier member of a
+    // self pair (their frame is recomputed on demand), frame slots for branch
+    // points (a joint whose parent is not the previous joint)
+    std::vector<int> cslot_of(L, -1), slot_of(L, -1);
+    int n_cslots = 0, n_slots = 0;
     int ng = 0;
     for (int i = 0; i < P;) {
         int j = i;
@@ -277,19 +277,27 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         G.la = static_cast<int16_t>(prs[i].la);
         G.p0 = static_cast<int16_t>(i);
         G.p1 = static_cast<int16_t>(j);
-        if (prs[i].la != prs[i].lb) need_slot(prs[i].la);
+        const int la = prs[i].la;
+        if (la != prs[i].lb && la > 0 && cslot_of[la] < 0) cslot_of[la] = n_cslots++;
         i = j;
     }
     for (int p = 0; p < P; ++p) rp.pairs[p] = PairC{static_cast<uint16_t>(prs[p].a), static_cast<uint16_t>(prs[p].b)};
-    // branch points: a joint whose parent is not the previous joint reads its
-    // parent's frame from the stash
-    for (int j = 0; j < D; ++j)
-        if (parent_link[j] != j && parent_link[j] != 0) need_slot(parent_link[j]);
-    for (int l = 0; l < L; ++l) rp.links[l].slot = static_cast<int16_t>(slot_of[l]);
+    for (int j = 0; j < D; ++j) {
+        const int pl = parent_link[j];
+        if (pl != j && pl != 0 && slot_of[pl] < 0) slot_of[pl] = n_slots++;
+    }
+    // joint path from the base to each link
+    std::vector<uint32_t> path(L, 0);
+    for (int j = 0; j < D; ++j) path[j + 1] = path[parent_link[j]] | (1u << j);
+    for (int l = 0; l < L; ++l) {
+        rp.links[l].slot = static_cast<int16_t>(slot_of[l]);
+        rp.links[l].cslot = static_cast<int16_t>(cslot_of[l]);
+        rp.links[l].path = static_cast<uint16_t>(path[l]);
+    }
     for (int g = 0; g < ng; ++g) {
         GroupC &G = rp.groups[g];
         const int lb = prs[G.p0].lb;
-        G.slot_a = static_cast<int16_t>(G.la == lb ? kSlotSameLink : (G.la == 0 ? kSlotBase : slot_of[G.la]));
+        G.slot_a = static_cast<int16_t>(G.la == lb ? kSlotSameLink : (G.la == 0 ? kSlotBase : cslot_of[G.la]));
     }
     for (int g = 0; g < ng;) {
         const int lb = prs[rp.groups[g].p0].lb;
@@ -306,6 +314,7 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     }
     rp.n_groups = ng;
     rp.n_slots = n_slots;
+    rp.n_cslots = n_cslots;
 
     ctx->robot = rp;
     ctx->sorted_of = sorted_of;
@@ -383,9 +392,9 @@ namespace {
 
 // Largest block (128, 64 or 32 threads) whose shared memory fits the
 // opt-in limit; returns false if none does.
-bool plan_block(vp_ctx *ctx, int n_slots, int *block, size_t *smem) {
+bool plan_block(vp_ctx *ctx, int *block, size_t *smem) {
     for (int b : {128, 64, 32}) {
-        const size_t s = smem_bytes(ctx->env, n_slots, b);
+        const size_t s = smem_bytes(ctx->env, ctx->robot.n_slots, ctx->robot.n_cslots, b);
         if (s <= ctx->smem_optin) {
             *block = b;
             *smem = s;
@@ -405,7 +414,7 @@ extern "C" vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float
     if (!q || !centres) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
     const int block = 128;
-    const size_t smem = static_cast<size_t>(ctx->robot.n_slots) * kStashFloats * block * sizeof(float);
+    const size_t smem = static_cast<size_t>(ctx->robot.n_slots) * kFrameFloats * block * sizeof(float);
     int bps = 0;
     cudaError_t e = prepare_fk(smem, block, &bps);
     if (e == cudaSuccess) {
@@ -425,7 +434,7 @@ extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, 
     DeviceGuard g(ctx->device);
     int block = 0;
     size_t smem = 0;
-    if (!plan_block(ctx, ctx->robot.n_slots, &block, &smem))
+    if (!plan_block(ctx, &block, &smem))
         return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
     int bps = 0;
     cudaError_t e = prepare_states(smem, block, &bps);
@@ -476,7 +485,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     }
     int block = 0;
     size_t smem = 0;
-    if (!plan_block(ctx, ctx->robot.n_slots, &block, &smem))
+    if (!plan_block(ctx, &block, &smem))
         return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
     int bps = 0;
     cudaError_t e = prepare_edges_plain(work != nullptr, smem, block, &bps);
@@ -487,7 +496,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
         const int D = ctx->robot.n_joints;
         for (int64_t i = 0; i < n_edges && e == cudaSuccess; ++i)
             e = launch_edges_plain(ctx->robot, ctx->env, q0 + i * D, q1 + i * D, counts ? counts + i : nullptr,
-                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_slots, 32), st);
+                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_slots, ctx->robot.n_cslots, 32), st);
         return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges (per edge)");
     }
     const int64_t need = (n_edges + wpb - 1) / wpb;

@@ -189,31 +189,55 @@ __device__ __forceinline__ bool stage_env(float4 *dst, const float4 *src, int n_
 }
 
 // ---------------------------------------------------------------------------
-// frame stash in shared memory: slot-major, lane-interleaved (conflict free)
+// per-lane stash in shared memory, slot-major and lane-interleaved (conflict
+// free): full frames of branch-point links (a joint whose parent is not the
+// previous joint reads its parent's frame here) and world centres of the
+// bounding spheres of links that are the earlier member of a self pair.
 
 struct Stash {
-    float *base;  // [n_slots][kStashFloats][blockDim.x]
-    int stride;   // blockDim.x
-    __device__ __forceinline__ float &at(int slot, int k) const {
-        return base[(slot * kStashFloats + k) * stride + threadIdx.x];
+    float *frames;   // [n_frame_slots][12][stride]
+    float *centres;  // [n_centre_slots][3][stride]
+    int stride;      // blockDim.x
+    __device__ __forceinline__ float &fr(int slot, int k) const {
+        return frames[(slot * 12 + k) * stride + threadIdx.x];
     }
-    __device__ __forceinline__ void store(int slot, const Fr &f, float3 cb) const {
-        at(slot, 0) = f.r0; at(slot, 1) = f.r1; at(slot, 2) = f.r2;
-        at(slot, 3) = f.r3; at(slot, 4) = f.r4; at(slot, 5) = f.r5;
-        at(slot, 6) = f.r6; at(slot, 7) = f.r7; at(slot, 8) = f.r8;
-        at(slot, 9) = f.px; at(slot, 10) = f.py; at(slot, 11) = f.pz;
-        at(slot, 12) = cb.x; at(slot, 13) = cb.y; at(slot, 14) = cb.z;
+    __device__ __forceinline__ float &ce(int slot, int k) const {
+        return centres[(slot * 3 + k) * stride + threadIdx.x];
     }
-    __device__ __forceinline__ void load(int slot, Fr &f) const {
-        f.r0 = at(slot, 0); f.r1 = at(slot, 1); f.r2 = at(slot, 2);
-        f.r3 = at(slot, 3); f.r4 = at(slot, 4); f.r5 = at(slot, 5);
-        f.r6 = at(slot, 6); f.r7 = at(slot, 7); f.r8 = at(slot, 8);
-        f.px = at(slot, 9); f.py = at(slot, 10); f.pz = at(slot, 11);
+    __device__ __forceinline__ void store_frame(int slot, const Fr &f) const {
+        fr(slot, 0) = f.r0; fr(slot, 1) = f.r1; fr(slot, 2) = f.r2;
+        fr(slot, 3) = f.r3; fr(slot, 4) = f.r4; fr(slot, 5) = f.r5;
+        fr(slot, 6) = f.r6; fr(slot, 7) = f.r7; fr(slot, 8) = f.r8;
+        fr(slot, 9) = f.px; fr(slot, 10) = f.py; fr(slot, 11) = f.pz;
+    }
+    __device__ __forceinline__ void load_frame(int slot, Fr &f) const {
+        f.r0 = fr(slot, 0); f.r1 = fr(slot, 1); f.r2 = fr(slot, 2);
+        f.r3 = fr(slot, 3); f.r4 = fr(slot, 4); f.r5 = fr(slot, 5);
+        f.r6 = fr(slot, 6); f.r7 = fr(slot, 7); f.r8 = fr(slot, 8);
+        f.px = fr(slot, 9); f.py = fr(slot, 10); f.pz = fr(slot, 11);
+    }
+    __device__ __forceinline__ void store_centre(int slot, float3 c) const {
+        ce(slot, 0) = c.x; ce(slot, 1) = c.y; ce(slot, 2) = c.z;
     }
     __device__ __forceinline__ float3 centre(int slot) const {
-        return make_float3(at(slot, 12), at(slot, 13), at(slot, 14));
+        return make_float3(ce(slot, 0), ce(slot, 1), ce(slot, 2));
     }
 };
+
+// Frame of link l recomputed from the base along its joint path (ascending
+// joint indices = root-to-leaf order).  Used when a self pair needs the
+// frame of an earlier link: recomputing it is cheaper than holding every
+// partner's frame in shared memory, which would cap the resident warps.
+template <class QF>
+__device__ __forceinline__ void recompute_frame(const RobotParams &P, int l, const QF &qf, Fr &g) {
+    fr_identity(g);
+    unsigned m = P.links[l].path;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        apply_joint(P.joints[j], qf(j), g);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // work counters (only in the counting variant)
@@ -249,11 +273,90 @@ __device__ __forceinline__ bool group_stop(unsigned mask, bool col) {
     return ANY ? __any_sync(mask, col) : __all_sync(mask, col);
 }
 
+// Coarse tests issued per warp vote, per primitive kind (independent
+// dependency chains for the schedulers to interleave).
+#ifndef VP_VOTE_MODE
+#define VP_VOTE_MODE 1  // 0: one REDUX.OR per chunk; 1: one vote, then a vote per primitive
+#endif
+#ifndef VP_UNROLL_SPHERE
+#define VP_UNROLL_SPHERE 8
+#endif
+#ifndef VP_UNROLL_CAPSULE
+#define VP_UNROLL_CAPSULE 8
+#endif
+#ifndef VP_UNROLL_CUBOID
+#define VP_UNROLL_CUBOID 8
+#endif
+
+// Primitive kinds: float4 words per primitive and the ball test.
+struct SphereKind {
+    static constexpr int kWords = 1;
+    __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) { return hit_sphere(c, r, o[0]); }
+};
+struct CapsuleKind {
+    static constexpr int kWords = 2;
+    __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
+        return hit_capsule(c, r, o[0], o[1]);
+    }
+};
+struct CuboidKind {
+    static constexpr int kWords = 4;
+    __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
+        return hit_cuboid(c, r, o[0], o[1], o[2], o[3]);
+    }
+};
+
+// One primitive kind against link l: coarse tests of the link's bounding
+// sphere on U primitives at a time (independent chains, one warp vote per
+// chunk), then fine tests of the link's spheres on each primitive some lane's
+// coarse sphere touched.  Returns the group's stop decision.
+template <class K, int U, bool ANY, bool STATS>
+__device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, const Fr &f, float3 cl, float Rl,
+                                         const float4 *prims, int n, unsigned mask, bool &col,
+                                         const WorkRef<STATS> &w, int fine_counter) {
+    for (int o0 = 0; o0 < n; o0 += U) {
+        unsigned bits = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (o0 + u < n) {
+                float4 ob[K::kWords];
+#pragma unroll
+                for (int k = 0; k < K::kWords; ++k) ob[k] = prims[(o0 + u) * K::kWords + k];
+                bits |= static_cast<unsigned>(K::hit(cl, Rl, ob)) << u;
+            }
+        }
+#if VP_VOTE_MODE == 0
+        unsigned any = __reduce_or_sync(mask, bits);
+#else
+        unsigned any = 0;
+        if (__any_sync(mask, bits != 0)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) any |= static_cast<unsigned>(__any_sync(mask, (bits >> u) & 1u)) << u;
+        }
+#endif
+        while (any) {
+            const int u = __ffs(any) - 1;
+            any &= any - 1;
+            const bool h = (bits >> u) & 1u;
+            float4 ob[K::kWords];
+#pragma unroll
+            for (int k = 0; k < K::kWords; ++k) ob[k] = prims[(o0 + u) * K::kWords + k];
+            w.add(fine_counter, L.s1 - L.s0);
+            for (int s = L.s0; s < L.s1; ++s) {
+                const float4 sp = P.spheres[s];
+                col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, ob);
+            }
+            if (group_stop<ANY>(mask, col)) return true;
+        }
+    }
+    return false;
+}
+
 // Check link l (posed as f) against the environment, coarse then fine, then
 // its self-collision groups.  `col` accumulates this lane's collision; the
 // return value is the group's stop decision.
-template <bool ANY, bool STATS>
-__device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr &f, float3 &cl,
+template <bool ANY, bool STATS, class QF>
+__device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr &f, float3 &cl, const QF &qf,
                                            const EnvSm &env, const Stash &stash, unsigned mask, bool &col,
                                            const WorkRef<STATS> &w) {
     const LinkC &L = P.links[l];
@@ -265,43 +368,14 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
         w.add(VP_WORK_COARSE_SPHERE, env.ns);
         w.add(VP_WORK_COARSE_CAPSULE, env.nc);
         w.add(VP_WORK_COARSE_CUBOID, env.nb);
-        for (int o = 0; o < env.ns; ++o) {
-            const float4 ob = env.sph[o];
-            const bool h = hit_sphere(cl, Rl, ob);
-            if (__any_sync(mask, h)) {
-                w.add(VP_WORK_FINE_SPHERE, L.s1 - L.s0);
-                for (int s = L.s0; s < L.s1; ++s) {
-                    const float4 sp = P.spheres[s];
-                    col |= h && hit_sphere(fr_apply(f, sp.x, sp.y, sp.z), sp.w, ob);
-                }
-                if (group_stop<ANY>(mask, col)) return true;
-            }
-        }
-        for (int o = 0; o < env.nc; ++o) {
-            const float4 a = env.cap[2 * o], b = env.cap[2 * o + 1];
-            const bool h = hit_capsule(cl, Rl, a, b);
-            if (__any_sync(mask, h)) {
-                w.add(VP_WORK_FINE_CAPSULE, L.s1 - L.s0);
-                for (int s = L.s0; s < L.s1; ++s) {
-                    const float4 sp = P.spheres[s];
-                    col |= h && hit_capsule(fr_apply(f, sp.x, sp.y, sp.z), sp.w, a, b);
-                }
-                if (group_stop<ANY>(mask, col)) return true;
-            }
-        }
-        for (int o = 0; o < env.nb; ++o) {
-            const float4 a0 = env.box[4 * o], a1 = env.box[4 * o + 1], a2 = env.box[4 * o + 2],
-                         hb = env.box[4 * o + 3];
-            const bool h = hit_cuboid(cl, Rl, a0, a1, a2, hb);
-            if (__any_sync(mask, h)) {
-                w.add(VP_WORK_FINE_CUBOID, L.s1 - L.s0);
-                for (int s = L.s0; s < L.s1; ++s) {
-                    const float4 sp = P.spheres[s];
-                    col |= h && hit_cuboid(fr_apply(f, sp.x, sp.y, sp.z), sp.w, a0, a1, a2, hb);
-                }
-                if (group_stop<ANY>(mask, col)) return true;
-            }
-        }
+        if (env_pass<SphereKind, VP_UNROLL_SPHERE, ANY, STATS>(P, L, f, cl, Rl, env.sph, env.ns, mask, col, w, VP_WORK_FINE_SPHERE))
+            return true;
+        if (env_pass<CapsuleKind, VP_UNROLL_CAPSULE, ANY, STATS>(P, L, f, cl, Rl, env.cap, env.nc, mask, col, w,
+                                                  VP_WORK_FINE_CAPSULE))
+            return true;
+        if (env_pass<CuboidKind, VP_UNROLL_CUBOID, ANY, STATS>(P, L, f, cl, Rl, env.box, env.nb, mask, col, w,
+                                                 VP_WORK_FINE_CUBOID))
+            return true;
     }
     // self pairs whose later link is l
     for (int g = L.g0; g < L.g1; ++g) {
@@ -321,7 +395,7 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
         if (__any_sync(mask, h)) {
             Fr fa;
             if (G.slot_a >= 0)
-                stash.load(G.slot_a, fa);
+                recompute_frame(P, G.la, qf, fa);
             else if (G.slot_a == kSlotBase)
                 fr_identity(fa);
             else
@@ -354,20 +428,23 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
     fr_identity(f);
     float3 cl = make_float3(0.f, 0.f, 0.f);
     w.add(VP_WORK_STATES, 1);
-    if (check_link<ANY, STATS>(P, 0, f, cl, env, stash, mask, col, w)) return col;
     const int D = P.n_joints;
-    for (int j = 0; j < D; ++j) {
-        const JointC &J = P.joints[j];
-        const int pm = (J.meta >> kMetaParentShift) & 0xFF;
-        if (pm == kParentBase)
-            fr_identity(f);
-        else if (pm != kParentPrev)
-            stash.load(pm, f);
-        apply_joint(J, qf(j), f);
-        const int l = j + 1;
-        if (check_link<ANY, STATS>(P, l, f, cl, env, stash, mask, col, w)) return col;
-        const int slot = P.links[l].slot;
-        if (slot >= 0) stash.store(slot, f, cl);
+    // link 0 is the base (identity frame); link l > 0 follows joint l - 1.
+    // One call site for check_link keeps the kernel's code compact.
+    for (int l = 0; l <= D; ++l) {
+        if (l > 0) {
+            const JointC &J = P.joints[l - 1];
+            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+            if (pm == kParentBase)
+                fr_identity(f);
+            else if (pm != kParentPrev)
+                stash.load_frame(pm, f);
+            apply_joint(J, qf(l - 1), f);
+        }
+        if (check_link<ANY, STATS>(P, l, f, cl, qf, env, stash, mask, col, w)) return col;
+        const LinkC &Lk = P.links[l];
+        if (Lk.slot >= 0) stash.store_frame(Lk.slot, f);
+        if (Lk.cslot >= 0) stash.store_centre(Lk.cslot, cl);
     }
     return col;
 }

@@ -18,7 +18,7 @@ struct SmemPlan {
     int blocks_per_sm;  // resident blocks per SM at this size
 };
 
-size_t smem_bytes(const EnvView &env, int n_slots, int block);
+size_t smem_bytes(const EnvView &env, int n_frame_slots, int n_centre_slots, int block);
 
 // Plain edge validation: one warp per edge, static grid-stride over edges.
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,

@@ -7,10 +7,11 @@
 
 namespace vp {
 
-size_t smem_bytes(const EnvView &env, int n_slots, int block) {
+size_t smem_bytes(const EnvView &env, int n_frame_slots, int n_centre_slots, int block) {
     const size_t warps = static_cast<size_t>((block + 31) / 32);
     return static_cast<size_t>(env.n_float4) * 16 + 16 + warps * 32 * sizeof(float) +
-           static_cast<size_t>(n_slots) * kStashFloats * block * sizeof(float);
+           static_cast<size_t>(n_frame_slots * kFrameFloats + n_centre_slots * kCentreFloats) * block *
+               sizeof(float);
 }
 
 // State count of an edge from its largest joint displacement (float32, IEEE
@@ -25,10 +26,10 @@ struct SmemCarve {
     float4 *env;
     uint64_t *bar;
     float *warp_buf;
-    float *stash;
+    Stash stash;
 };
 
-__device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &env) {
+__device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &env, const RobotParams &P) {
     SmemCarve c;
     size_t off = static_cast<size_t>(env.n_float4) * 16;
     c.env = reinterpret_cast<float4 *>(smem);
@@ -36,7 +37,10 @@ __device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &e
     off += 16;
     c.warp_buf = reinterpret_cast<float *>(smem + off);
     off += static_cast<size_t>((blockDim.x + 31) / 32) * 32 * sizeof(float);
-    c.stash = reinterpret_cast<float *>(smem + off);
+    c.stash.frames = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>(P.n_slots) * kFrameFloats * blockDim.x * sizeof(float);
+    c.stash.centres = reinterpret_cast<float *>(smem + off);
+    c.stash.stride = static_cast<int>(blockDim.x);
     return c;
 }
 
@@ -73,10 +77,10 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
                                                           const long long E, uint8_t *__restrict__ valid,
                                                           unsigned *status, unsigned long long *work) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemCarve sc = carve(smem, env);
+    const SmemCarve sc = carve(smem, env, P);
     if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
     const EnvSm es = env_view(sc.env, env);
-    const Stash stash{sc.stash, static_cast<int>(blockDim.x)};
+    const Stash &stash = sc.stash;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     float *wq0 = sc.warp_buf + wib * 32;
     float *wdq = wq0 + 16;
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
                 const float t = static_cast<float>(i) * inv;
                 const WorkRef<STATS> w{&wk, real};
                 const bool c = pose_and_check<true, STATS>(
-                    P, [&](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, kFull, w);
+                    P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, kFull, w);
                 if (__any_sync(kFull, c)) {
                     collided = true;
                     break;
@@ -150,10 +154,10 @@ __global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ Rob
                                                      const float *__restrict__ q, const long long N,
                                                      uint8_t *__restrict__ valid, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemCarve sc = carve(smem, env);
+    const SmemCarve sc = carve(smem, env, P);
     if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
     const EnvSm es = env_view(sc.env, env);
-    const Stash stash{sc.stash, static_cast<int>(blockDim.x)};
+    const Stash &stash = sc.stash;
     const int lane = threadIdx.x & 31;
     const int D = P.n_joints;
     const long long step = static_cast<long long>(gridDim.x) * blockDim.x;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ Rob
         bool fin = true;
         for (int j = 0; j < D; ++j) fin &= isfinite(qi[j]);
         const WorkRef<false> w{nullptr, false};
-        const bool c = pose_and_check<false, false>(P, [&](int j) { return qi[j]; }, es, stash, kFull, w);
+        const bool c = pose_and_check<false, false>(P, [qi](int j) { return qi[j]; }, es, stash, kFull, w);
         if (real) valid[i] = (c || !fin) ? 0 : 1;
     }
 }
@@ -175,7 +179,10 @@ __global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ Rob
 __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
                                                  const long long N, float *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Stash stash{reinterpret_cast<float *>(smem), static_cast<int>(blockDim.x)};
+    Stash stash;
+    stash.frames = reinterpret_cast<float *>(smem);
+    stash.centres = nullptr;
+    stash.stride = static_cast<int>(blockDim.x);
     const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int D = P.n_joints, S = P.n_spheres;
@@ -190,9 +197,9 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ RobotPa
             if (pm == kParentBase)
                 fr_identity(f);
             else if (pm != kParentPrev)
-                stash.load(pm, f);
+                stash.load_frame(pm, f);
             apply_joint(J, qi[l - 1], f);
-            if (P.links[l].slot >= 0) stash.store(P.links[l].slot, f, make_float3(0.f, 0.f, 0.f));
+            if (P.links[l].slot >= 0) stash.store_frame(P.links[l].slot, f);
         }
         const LinkC &L = P.links[l];
         for (int s = L.s0; s < L.s1; ++s) {

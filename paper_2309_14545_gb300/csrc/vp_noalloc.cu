@@ -202,7 +202,7 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     int block = 0;
     size_t smem = 0;
     for (int b : {128, 64, 32}) {
-        const size_t s = smem_bytes(ev, rp.n_slots, b);
+        const size_t s = smem_bytes(ev, rp.n_slots, rp.n_cslots, b);
         if (s <= ds->smem_optin) {
             block = b;
             smem = s;

@@ -28,15 +28,15 @@ constexpr int kAxisX = 0, kAxisY = 1, kAxisZ = 2, kAxisGeneral = 3;
 constexpr int kMetaParentShift = 8;  // 8 bits: parent frame source
 constexpr int kParentPrev = 0xFF;    // the previous joint's link (kept in registers)
 constexpr int kParentBase = 0xFE;    // the base (identity)
-// any other value: the stash slot holding the parent link's frame
+// any other value: the frame-stash slot holding the parent link's frame
 
-// GroupC::slot_a special values
+// GroupC::slot_a: the centre-stash slot of the earlier link, or
 constexpr int kSlotSameLink = -1;  // both spheres on the current link
 constexpr int kSlotBase = -2;      // earlier link is the base (identity frame)
 
-// Floats kept per stash slot: frame [R row-major | p] (12) + world centre of
-// the link's bounding sphere (3).
-constexpr int kStashFloats = 15;
+// Shared-memory floats per lane for each kind of stash slot.
+constexpr int kFrameFloats = 12;   // frame [R row-major | p] of a branch-point link
+constexpr int kCentreFloats = 3;   // world centre of a self-pair partner's bounding sphere
 
 // Conservative inflation of every link bounding sphere (m): covers float32
 // rounding in the coarse test so a coarse miss never hides a fine hit.
@@ -49,16 +49,18 @@ struct JointC {  // 64 bytes
 };
 
 struct LinkC {  // 32 bytes
-    float4 bs;      // bounding sphere: centre (link frame), radius (+eps); radius < 0: no spheres
+    float4 bs;       // bounding sphere: centre (link frame), radius (+eps); radius < 0: no spheres
     int16_t s0, s1;  // fine spheres [s0, s1) in sorted order
     int16_t g0, g1;  // self groups [g0, g1) checked once this link is posed
-    int16_t slot;    // stash slot for this link's frame, -1 if none
-    int16_t pad[3];
+    int16_t slot;    // frame-stash slot (branch point), -1 if none
+    int16_t cslot;   // centre-stash slot (earlier self-pair partner), -1 if none
+    uint16_t path;   // joints from the base to this link (bit j = joint j)
+    int16_t pad;
 };
 
 struct GroupC {      // one link pair (la < lb) and its sphere pairs
     int16_t la;      // earlier link
-    int16_t slot_a;  // stash slot of la, or kSlotSameLink / kSlotBase
+    int16_t slot_a;  // centre-stash slot of la, or kSlotSameLink / kSlotBase
     int16_t p0, p1;  // pairs [p0, p1)
 };
 
@@ -67,8 +69,10 @@ struct PairC {
 };
 
 struct RobotParams {
-    int n_joints, n_links, n_spheres, n_pairs, n_groups, n_slots;
-    int pad0, pad1;
+    int n_joints, n_links, n_spheres, n_pairs, n_groups;
+    int n_slots;    // frame-stash slots
+    int n_cslots;   // centre-stash slots
+    int pad0;
     JointC joints[kMaxJoints];
     LinkC links[kMaxLinks];
     float4 spheres[kMaxSpheres];  // local centre, radius (sorted by link)
