@@ -261,7 +261,7 @@ def run_native(args):
         if mode == vp.VP_MODE_BATCHED:
             val.autotune(q0, q1, counts, w.res, stream=stream)
         # work counters (untimed): the FLOP numerator of the roofline
-        _, work = val.validate_edges_work(q0, q1, counts, w.res, stream=stream)
+        _, work = val.validate_edges_work(q0, q1, counts, w.res, mode=mode, stream=stream)
         work = work.cpu().numpy()
     flops = work_flops(work, w.robot)
 

@@ -174,10 +174,12 @@ vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float re
 vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                             float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
 
-/* Work counters for the FLOP model: the plain edge validation with counters
- * of the work done (VP_WORK_* indices) added into `work` (device uint64
- * [VP_WORK_N]; the caller zeroes it).  Only states of the edge are counted
- * (a lane parked on a repeated state is not). */
+/* Work counters for the FLOP model: edge validation in `mode` (VP_MODE_PLAIN
+ * or VP_MODE_BATCHED, the latter launched directly rather than from its
+ * graph) with counters of the work done (VP_WORK_* indices) added into `work`
+ * (device uint64 [VP_WORK_N]; the caller zeroes it).  Only lanes holding a
+ * state of a live edge are counted (a lane parked on a repeated state, or in
+ * a finished lane group, is not). */
 enum {
     VP_WORK_STATES = 0,     /* states posed (FK run)                          */
     VP_WORK_LINK_CENTRES,   /* link bounding-sphere centres computed          */
@@ -193,7 +195,7 @@ enum {
     VP_WORK_N = 16
 };
 vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
-                                 float resolution, int64_t n_edges, uint8_t *valid, uint64_t *work,
+                                 float resolution, int64_t n_edges, uint8_t *valid, int mode, uint64_t *work,
                                  void *stream);
 
 /* Penetration cost (an addition beside the paper, which defines none):

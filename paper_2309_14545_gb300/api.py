@@ -64,10 +64,10 @@ class Validator:
         vp.vp_validate_edges(self.ctx, q0, q1, counts, float(resolution), out, mode, stream)
         return out
 
-    def validate_edges_work(self, q0, q1, counts=None, resolution=1.0 / 32.0, stream=None):
+    def validate_edges_work(self, q0, q1, counts=None, resolution=1.0 / 32.0, mode=vp.VP_MODE_PLAIN, stream=None):
         out = torch.empty(q0.shape[0], dtype=torch.uint8, device=self._dev())
         work = torch.zeros(vp.VP_WORK_N, dtype=torch.int64, device=self._dev())
-        vp.vp_validate_edges_work(self.ctx, q0, q1, counts, float(resolution), out, work, stream)
+        vp.vp_validate_edges_work(self.ctx, q0, q1, counts, float(resolution), out, mode, work, stream)
         return out, work
 
     def autotune(self, q0, q1, counts=None, resolution=1.0 / 32.0, stream=None):

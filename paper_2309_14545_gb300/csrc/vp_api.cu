@@ -475,11 +475,12 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     if (!q0 || !q1 || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (mode == VP_MODE_BATCHED && !work) {
+    if (mode == VP_MODE_BATCHED) {
         BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
                       ctx->num_sms, ctx->smem_optin, st};
         std::string msg;
-        const int rc = batched_validate(ctx->batched, a, &msg);
+        const int rc = work ? batched_work(ctx->batched, a, reinterpret_cast<unsigned long long *>(work), &msg)
+                            : batched_validate(ctx->batched, a, &msg);
         if (rc == 0) return VP_OK;
         return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "batched: %s", msg.c_str());
     }
@@ -512,10 +513,11 @@ extern "C" vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float
 }
 
 extern "C" vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
-                                            float resolution, int64_t n_edges, uint8_t *valid, uint64_t *work,
-                                            void *stream) {
+                                            float resolution, int64_t n_edges, uint8_t *valid, int mode,
+                                            uint64_t *work, void *stream) {
     if (ctx && !work) return fail(ctx, VP_ERR_ARG, "work is NULL");
-    return validate_edges_impl(ctx, q0, q1, counts, resolution, n_edges, valid, VP_MODE_PLAIN, work, stream);
+    if (ctx && mode == VP_MODE_PER_EDGE) return fail(ctx, VP_ERR_ARG, "no work counters for VP_MODE_PER_EDGE");
+    return validate_edges_impl(ctx, q0, q1, counts, resolution, n_edges, valid, mode, work, stream);
 }
 
 extern "C" vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin, float *cost,

@@ -1,8 +1,575 @@
+// Batched edge validation for batches of uneven edge lengths.
+//
+// 1. bucket_count_kernel: state count k_e of every edge (explicit or from the
+//    resolution), bucket = ceil(log2 k) class ([2,4], [5,8], ..., [257,512],
+//    >512), block-aggregated histogram.  Malformed edges are answered here.
+// 2. bucket_scatter_kernel: a permutation listing edges bucket by bucket,
+//    longest bucket first (longest-processing-time order for the queue).
+// 3. edges_batched_kernel: persistent; each warp pops work items from one
+//    global counter.  A work item of bucket b packs 32/G_b edges into lane
+//    groups of G_b lanes; the groups run the raked check in lockstep and the
+//    warp leaves a state as soon as every group has a collision or is done.
+// The three launches (plus the counter reset) are captured once into a CUDA
+// graph per buffer set and replayed.  G_b comes from the autotuner, which
+// times each bucket's sample edges with every group size and keeps the
+// fastest (cached per robot, environment and length profile).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
 #include "vp_batched.h"
+#include "vp_device.cuh"
 
 namespace vp {
-int batched_validate(BatchedState &, const BatchedArgs &, std::string *msg) { *msg = "not built"; return 2; }
-int batched_autotune(BatchedState &, const BatchedArgs &, std::string *msg) { *msg = "not built"; return 2; }
-void batched_invalidate(BatchedState &) {}
-void batched_release(BatchedState &) {}
+
+namespace {
+
+constexpr int kNB = 9;           // length buckets
+constexpr int kBlock = 128;      // threads per block of the persistent kernel
+constexpr int kCtrlHist = 0;     // ctrl[0..8]   edges per bucket
+constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
+constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
+constexpr int kCtrlInts = 64;
+constexpr unsigned long long kWatchdogNs = 20ull * 1000 * 1000 * 1000;  // 20 s per launch
+
+struct BatchPlan {
+    int G[kNB];            // lanes per edge, per bucket
+    int edge_off[kNB + 1]; // bucket b's edges are perm[edge_off[b], edge_off[b+1]) (when !from_hist)
+    int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
+};
+
+__host__ __device__ __forceinline__ int bucket_of(int k) {
+    // ceil(log2 k) - 2, clamped: [2,4] -> 0, [5,8] -> 1, ..., [257,512] -> 7, > 512 -> 8
+    int c = 0;
+    unsigned v = static_cast<unsigned>(k - 1);
+    while (v) {
+        ++c;
+        v >>= 1;
+    }
+    return min(max(c - 2, 0), kNB - 1);
+}
+
+// Exclusive offsets of the buckets in processing order (longest first).
+__device__ __forceinline__ void offsets_from_hist(const int *hist, int *off) {
+    int acc = 0;
+    for (int b = kNB - 1; b >= 0; --b) {
+        off[b] = acc;
+        acc += hist[b];
+    }
+    off[kNB] = acc;  // total; off[b] + hist[b] is bucket b's end
+}
+
+__device__ __forceinline__ int count_from_dmax_b(float dmax, float res) {
+    const float steps = ceilf(__fdiv_rn(dmax, res));
+    if (!(steps <= static_cast<float>(VP_MAX_STEPS))) return -1;
+    return max(2, static_cast<int>(steps) + 1);
+}
+
+__global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, const float *__restrict__ q1,
+                                    const int32_t *__restrict__ counts, const float res, const long long E,
+                                    int32_t *__restrict__ kbuf, uint8_t *__restrict__ valid, unsigned *status,
+                                    int *ctrl) {
+    __shared__ int hist[kNB];
+    if (threadIdx.x < kNB) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < E) {
+        float dmax = 0.f;
+        bool fin = true;
+        for (int j = 0; j < D; ++j) {
+            const float a = q0[e * D + j], b = q1[e * D + j];
+            fin &= isfinite(a) && isfinite(b);
+            if (fin) dmax = fmaxf(dmax, fabsf(b - a));
+        }
+        int k = -1;
+        if (counts != nullptr) {
+            k = counts[e];
+            if (k < 2) {
+                atomicOr(status, VP_DEVERR_COUNT);
+                k = -1;
+            }
+        } else if (fin) {
+            k = count_from_dmax_b(dmax, res);
+            if (k < 0) atomicOr(status, VP_DEVERR_LENGTH);
+        }
+        if (!fin) k = -1;
+        kbuf[e] = k;
+        if (k < 0)
+            valid[e] = 0;
+        else
+            atomicAdd(&hist[bucket_of(k)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNB && hist[threadIdx.x]) atomicAdd(&ctrl[kCtrlHist + threadIdx.x], hist[threadIdx.x]);
+}
+
+__global__ void bucket_scatter_kernel(const long long E, const int32_t *__restrict__ kbuf,
+                                      int32_t *__restrict__ perm, int *ctrl) {
+    __shared__ int cnt[kNB], base[kNB], off[kNB + 1];
+    if (threadIdx.x == 0) offsets_from_hist(ctrl + kCtrlHist, off);
+    if (threadIdx.x < kNB) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int b = -1, r = 0;
+    if (e < E) {
+        const int k = kbuf[e];
+        if (k >= 2) {
+            b = bucket_of(k);
+            r = atomicAdd(&cnt[b], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNB && cnt[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&ctrl[kCtrlCursor + threadIdx.x], cnt[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) perm[off[b] + base[b] + r] = static_cast<int32_t>(e);
+}
+
+// Persistent validation of bucketed edges; see the file comment.  STATS adds
+// the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
+template <bool STATS>
+__global__ void __launch_bounds__(kBlock) edges_batched_kernel(
+    const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
+    const float *__restrict__ q1, const int32_t *__restrict__ kbuf, const int32_t *__restrict__ perm,
+    const BatchPlan plan, uint8_t *__restrict__ valid, unsigned *status, int *ctrl, unsigned long long *work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_edge_lo[kNB], s_edge_hi[kNB], s_item_end[kNB];
+    __shared__ int s_items;
+    size_t off = static_cast<size_t>(env.n_float4) * 16;
+    float4 *env_sm = reinterpret_cast<float4 *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
+    off += 16;
+    float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
+    off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
+    Stash stash;
+    stash.frames = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>(P.n_slots) * kFrameFloats * kBlock * sizeof(float);
+    stash.centres = reinterpret_cast<float *>(smem + off);
+    stash.stride = kBlock;
+
+    if (threadIdx.x == 0) {
+        int eo[kNB + 1];
+        if (plan.from_hist) {
+            offsets_from_hist(ctrl + kCtrlHist, eo);
+            for (int b = 0; b < kNB; ++b) {
+                s_edge_lo[b] = eo[b];
+                s_edge_hi[b] = eo[b] + ctrl[kCtrlHist + b];
+            }
+        } else {
+            for (int b = 0; b < kNB; ++b) {
+                s_edge_lo[b] = plan.edge_off[b];
+                s_edge_hi[b] = plan.edge_off[b + 1];
+            }
+        }
+        // work items in processing order: longest bucket first
+        int items = 0;
+        for (int b = kNB - 1; b >= 0; --b) {
+            const int per = 32 / plan.G[b];
+            items += (s_edge_hi[b] - s_edge_lo[b] + per - 1) / per;
+            s_item_end[b] = items;
+        }
+        s_items = items;
+    }
+    __syncthreads();
+    if (!stage_env(env_sm, env.data, env.n_float4, bar, status)) return;
+    const EnvSm es{env_sm, env_sm + env.ns, env_sm + env.ns + 2 * env.nc, env.ns, env.nc, env.nb};
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int D = P.n_joints;
+    float *wbuf = gbuf + wib * 8 * 32;
+    const uint64_t t_start = global_ns();
+    Work wk;
+    if (STATS) {
+#pragma unroll
+        for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
+    }
+
+    while (true) {
+        int item = 0;
+        if (lane == 0) {
+            if (global_ns() - t_start > kWatchdogNs) {
+                atomicOr(status, VP_DEVERR_TIMEOUT);
+                item = -1;
+            } else {
+                item = atomicAdd(&ctrl[kCtrlQueue], 1);
+            }
+        }
+        item = __shfl_sync(kFull, item, 0);
+        if (item < 0 || item >= s_items) break;
+        int b = kNB - 1;
+        while (item >= s_item_end[b]) --b;
+        const int first_item = (b == kNB - 1) ? 0 : s_item_end[b + 1];
+        const int G = plan.G[b];
+        const int per = 32 / G;
+        const int g = lane / G, j = lane - g * G;
+        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
+        const int slot = s_edge_lo[b] + (item - first_item) * per + g;
+        const bool has_edge = g < per && slot < s_edge_hi[b];
+        const int e = has_edge ? perm[slot] : 0;
+        int k = has_edge ? kbuf[e] : 2;
+        float *gq0 = wbuf + g * 32, *gdq = gq0 + 16;
+        __syncwarp();
+        if (has_edge) {
+            for (int d = j; d < D; d += G) {
+                const float a = q0[static_cast<long long>(e) * D + d];
+                gq0[d] = a;
+                gdq[d] = q1[static_cast<long long>(e) * D + d] - a;
+            }
+        } else {
+            for (int d = j; d < 16; d += G) {
+                gq0[d] = 0.f;
+                gdq[d] = 0.f;
+            }
+        }
+        __syncwarp();
+        const int R = (k + G - 1) / G;
+        const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
+        const int R_max = __reduce_max_sync(kFull, has_edge ? R : 0);
+        bool done = !has_edge;
+        for (int r = 0; r < R_max; ++r) {
+            int i = j * R + r;
+            const WorkRef<STATS> w{&wk, !done && i < k};
+            if (i >= k) i = k - 1;
+            const float t = static_cast<float>(i) * inv;
+            const bool c = pose_and_check<kStopGroups, STATS>(
+                P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w);
+            const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
+            if (!done && (gcol || r == R - 1)) {
+                if (j == 0) {
+                    valid[e] = gcol ? 0 : 1;
+                    if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
+                }
+                done = true;
+            }
+            if (__all_sync(kFull, done)) break;
+        }
+        if constexpr (STATS) {
+#pragma unroll
+            for (int c = 0; c < VP_WORK_N; ++c) {
+                const unsigned sum = __reduce_add_sync(kFull, wk.v[c]);
+                if (lane == 0 && sum) atomicAdd(work + c, static_cast<unsigned long long>(sum));
+                wk.v[c] = 0;
+            }
+        }
+    }
+}
+
+size_t batched_smem(const EnvView &env, const RobotParams &P) {
+    return static_cast<size_t>(env.n_float4) * 16 + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
+           static_cast<size_t>(P.n_slots * kFrameFloats + P.n_cslots * kCentreFloats) * kBlock * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct TuneKey {
+    std::vector<unsigned char> robot;
+    int ns, nc, nb, sms;
+    std::vector<int> profile;  // length histogram, coarse
+    bool operator<(const TuneKey &o) const {
+        return std::tie(robot, ns, nc, nb, sms, profile) < std::tie(o.robot, o.ns, o.nc, o.nb, o.sms, o.profile);
+    }
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::vector<int>> g_tune_cache;
+
+struct Impl {
+    int32_t *kbuf = nullptr, *perm = nullptr;
+    int *ctrl = nullptr;
+    int64_t cap = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // graph key
+    const void *k_q0 = nullptr, *k_q1 = nullptr, *k_counts = nullptr, *k_valid = nullptr;
+    int64_t k_E = -1;
+    float k_res = 0.f;
+    int G[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+    bool tuned = false;
+};
+
+Impl *impl_of(BatchedState &st) {
+    if (!st.impl) st.impl = new Impl();
+    return static_cast<Impl *>(st.impl);
+}
+
+void drop_graph(Impl *im) {
+    if (im->exec) cudaGraphExecDestroy(im->exec);
+    im->exec = nullptr;
+    im->k_E = -1;
+}
+
+int set_err(std::string *msg, const char *what, cudaError_t e) {
+    *msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return 2;
+}
+
+int ensure_capacity(Impl *im, int64_t E, std::string *msg) {
+    if (!im->ctrl) {
+        cudaError_t e = cudaMalloc(&im->ctrl, kCtrlInts * sizeof(int));
+        if (e != cudaSuccess) return set_err(msg, "cudaMalloc ctrl", e);
+    }
+    if (!im->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&im->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_err(msg, "cudaStreamCreate", e);
+    }
+    if (E <= im->cap) return 0;
+    drop_graph(im);
+    if (im->kbuf) cudaFree(im->kbuf);
+    if (im->perm) cudaFree(im->perm);
+    im->kbuf = im->perm = nullptr;
+    im->cap = 0;
+    const int64_t n = std::max<int64_t>(E, 1 << 16);
+    cudaError_t e = cudaMalloc(&im->kbuf, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&im->perm, n * sizeof(int32_t));
+    if (e != cudaSuccess) return set_err(msg, "cudaMalloc scratch", e);
+    im->cap = n;
+    return 0;
+}
+
+int prepare_kernel(const BatchedArgs &a, size_t *smem, int *grid, std::string *msg) {
+    *smem = batched_smem(*a.env, *a.robot);
+    if (*smem > a.smem_optin) {
+        *msg = "environment and frame stash exceed shared memory";
+        return 1;
+    }
+    cudaError_t e = cudaFuncSetAttribute(edges_batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(*smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(edges_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(*smem));
+    int bps = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, edges_batched_kernel<false>, kBlock, *smem);
+    if (e != cudaSuccess) return set_err(msg, "batched kernel attributes", e);
+    if (bps < 1) {
+        *msg = "batched kernel cannot be resident";
+        return 1;
+    }
+    *grid = bps * a.num_sms;
+    return 0;
+}
+
+// Enqueue the whole pipeline on stream s (also used under capture).
+cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_t smem, int grid, cudaStream_t s,
+                    uint8_t *valid, unsigned long long *work = nullptr) {
+    const int D = a.robot->n_joints;
+    cudaError_t e = cudaMemsetAsync(im->ctrl, 0, kCtrlInts * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = static_cast<unsigned>((a.E + 255) / 256);
+    bucket_count_kernel<<<nb, 256, 0, s>>>(D, a.q0, a.q1, a.counts, a.res, a.E, im->kbuf, valid, a.status, im->ctrl);
+    bucket_scatter_kernel<<<nb, 256, 0, s>>>(a.E, im->kbuf, im->perm, im->ctrl);
+    if (work)
+        edges_batched_kernel<true><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf, im->perm, plan,
+                                                              valid, a.status, im->ctrl, work);
+    else
+        edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf, im->perm,
+                                                               plan, valid, a.status, im->ctrl, nullptr);
+    return cudaGetLastError();
+}
+
+BatchPlan plan_from(const Impl *im) {
+    BatchPlan p;
+    std::memset(&p, 0, sizeof(p));
+    for (int b = 0; b < kNB; ++b) p.G[b] = im->G[b];
+    p.from_hist = 1;
+    return p;
+}
+
+}  // namespace
+
+int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
+    Impl *im = impl_of(st);
+    int rc = ensure_capacity(im, a.E, msg);
+    if (rc) return rc;
+    size_t smem = 0;
+    int grid = 0;
+    rc = prepare_kernel(a, &smem, &grid, msg);
+    if (rc) return rc;
+    const bool same = im->exec && im->k_q0 == a.q0 && im->k_q1 == a.q1 && im->k_counts == a.counts &&
+                      im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res;
+    if (!same) {
+        drop_graph(im);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(im->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return set_err(msg, "begin capture", e);
+        cudaError_t e2 = enqueue(im, a, plan_from(im), smem, grid, im->cap_stream, a.valid);
+        e = cudaStreamEndCapture(im->cap_stream, &graph);
+        if (e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return set_err(msg, "capture", e2);
+        }
+        if (e != cudaSuccess) return set_err(msg, "end capture", e);
+        e = cudaGraphInstantiate(&im->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            im->exec = nullptr;
+            return set_err(msg, "instantiate", e);
+        }
+        im->k_q0 = a.q0;
+        im->k_q1 = a.q1;
+        im->k_counts = a.counts;
+        im->k_valid = a.valid;
+        im->k_E = a.E;
+        im->k_res = a.res;
+    }
+    cudaError_t e = cudaGraphLaunch(im->exec, a.stream);
+    return e == cudaSuccess ? 0 : set_err(msg, "graph launch", e);
+}
+
+int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *work, std::string *msg) {
+    Impl *im = impl_of(st);
+    int rc = ensure_capacity(im, a.E, msg);
+    if (rc) return rc;
+    size_t smem = 0;
+    int grid = 0;
+    rc = prepare_kernel(a, &smem, &grid, msg);
+    if (rc) return rc;
+    const cudaError_t e = enqueue(im, a, plan_from(im), smem, grid, a.stream, a.valid, work);
+    return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
+}
+
+int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
+    Impl *im = impl_of(st);
+    const int64_t S = std::min<int64_t>(a.E, 1 << 17);  // tuning sample: the first edges
+    int rc = ensure_capacity(im, S, msg);
+    if (rc) return rc;
+    size_t smem = 0;
+    int grid = 0;
+    rc = prepare_kernel(a, &smem, &grid, msg);
+    if (rc) return rc;
+    cudaStream_t s = a.stream;
+    uint8_t *tv = nullptr;
+    cudaError_t e = cudaMalloc(&tv, S);
+    if (e != cudaSuccess) return set_err(msg, "cudaMalloc tuning output", e);
+    // bucket the sample once
+    const unsigned nb = static_cast<unsigned>((S + 255) / 256);
+    e = cudaMemsetAsync(im->ctrl, 0, kCtrlInts * sizeof(int), s);
+    if (e == cudaSuccess) {
+        bucket_count_kernel<<<nb, 256, 0, s>>>(a.robot->n_joints, a.q0, a.q1, a.counts, a.res, S, im->kbuf, tv,
+                                               a.status, im->ctrl);
+        bucket_scatter_kernel<<<nb, 256, 0, s>>>(S, im->kbuf, im->perm, im->ctrl);
+        e = cudaGetLastError();
+    }
+    int hist[kNB] = {0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hist, im->ctrl + kCtrlHist, sizeof(hist), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(tv);
+        return set_err(msg, "tuning bucket pass", e);
+    }
+    TuneKey key;
+    key.robot.assign(reinterpret_cast<const unsigned char *>(a.robot),
+                     reinterpret_cast<const unsigned char *>(a.robot) + sizeof(RobotParams));
+    key.ns = a.env->ns;
+    key.nc = a.env->nc;
+    key.nb = a.env->nb;
+    key.sms = a.num_sms;
+    for (int b = 0; b < kNB; ++b) key.profile.push_back(hist[b] == 0 ? 0 : 1 + (20 * hist[b]) / static_cast<int>(S));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            for (int b = 0; b < kNB; ++b) im->G[b] = it->second[b];
+            im->tuned = true;
+            drop_graph(im);
+            cudaFree(tv);
+            return 0;
+        }
+    }
+    int off[kNB + 1];
+    {
+        int acc = 0;
+        for (int b = kNB - 1; b >= 0; --b) {
+            off[b] = acc;
+            acc += hist[b];
+        }
+        off[kNB] = acc;
+    }
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const int options[4] = {4, 8, 16, 32};
+    for (int b = 0; b < kNB && e == cudaSuccess; ++b) {
+        if (hist[b] < 64) continue;  // too few to time: keep the default
+        float best = 1e30f;
+        int best_g = im->G[b];
+        for (int G : options) {
+            BatchPlan p;
+            std::memset(&p, 0, sizeof(p));
+            for (int c = 0; c < kNB; ++c) {
+                p.G[c] = G;
+                p.edge_off[c] = 0;
+            }
+            p.edge_off[kNB] = 0;
+            // only bucket b: every other bucket empty
+            for (int c = 0; c <= kNB; ++c) p.edge_off[c] = (c <= b) ? off[b] : off[b] + hist[b];
+            p.from_hist = 0;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
+                if (e != cudaSuccess) break;
+                cudaEventRecord(t0, s);
+                edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf,
+                                                                       im->perm, p, tv, a.status, im->ctrl, nullptr);
+                cudaEventRecord(t1, s);
+                e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best) {
+                best = ms_min;
+                best_g = G;
+            }
+        }
+        im->G[b] = best_g;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFree(tv);
+    if (e != cudaSuccess) return set_err(msg, "tuning runs", e);
+    im->tuned = true;
+    drop_graph(im);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = std::vector<int>(im->G, im->G + kNB);
+    }
+    return 0;
+}
+
+void batched_invalidate(BatchedState &st) {
+    if (!st.impl) return;
+    Impl *im = static_cast<Impl *>(st.impl);
+    drop_graph(im);
+    im->tuned = false;
+    const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+    for (int b = 0; b < kNB; ++b) im->G[b] = defaults[b];
+}
+
+void batched_release(BatchedState &st) {
+    if (!st.impl) return;
+    Impl *im = static_cast<Impl *>(st.impl);
+    drop_graph(im);
+    if (im->kbuf) cudaFree(im->kbuf);
+    if (im->perm) cudaFree(im->perm);
+    if (im->ctrl) cudaFree(im->ctrl);
+    if (im->cap_stream) cudaStreamDestroy(im->cap_stream);
+    delete im;
+    st.impl = nullptr;
+}
+
+int batched_tiling(const BatchedState &st, int *G, int n) {
+    const Impl *im = static_cast<const Impl *>(st.impl);
+    const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+    for (int b = 0; b < n && b < kNB; ++b) G[b] = im ? im->G[b] : defaults[b];
+    return kNB;
+}
+
 }  // namespace vp

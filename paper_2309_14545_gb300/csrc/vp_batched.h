@@ -31,7 +31,11 @@ struct BatchedState {
 // 0 = ok, 1 = capacity, 2 = CUDA error (message in *msg)
 int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg);
 int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg);
+// Batched validation without the graph, adding work counters into `work`.
+int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *work, std::string *msg);
 void batched_invalidate(BatchedState &st);
 void batched_release(BatchedState &st);
+// Lanes per edge chosen for each length bucket; returns the bucket count.
+int batched_tiling(const BatchedState &st, int *G, int n);
 
 }  // namespace vp

@@ -265,19 +265,34 @@ struct EnvSm {
     int ns, nc, nb;
 };
 
-// Early-exit rule of the group of lanes sharing `mask`:
-//   ANY = true  (edges): stop as soon as any lane of the group collides;
-//   ANY = false (independent states): stop once every lane has collided.
-template <bool ANY>
-__device__ __forceinline__ bool group_stop(unsigned mask, bool col) {
-    return ANY ? __any_sync(mask, col) : __all_sync(mask, col);
+// Early-exit rules.  Every vote spans the full warp; a warp may hold one
+// edge (kStopAny: stop as soon as any lane collides), independent states
+// (kStopAll: stop once every lane has collided) or several edges in lane
+// groups (kStopGroups: stop once every group has a colliding lane or is idle,
+// i.e. already finished with its edge).
+enum : int { kStopAny = 0, kStopAll = 1, kStopGroups = 2 };
+
+struct Ctl {
+    unsigned gmask;  // lanes of this lane's group (kStopGroups)
+    bool idle;       // this lane's group is finished and must not drive the warp
+};
+
+template <int MODE>
+__device__ __forceinline__ bool group_stop(const Ctl &c, bool col) {
+    if (MODE == kStopAny) return __any_sync(kFull, col);
+    if (MODE == kStopAll) return __all_sync(kFull, col);
+    const bool gcol = (__ballot_sync(kFull, col) & c.gmask) != 0u;
+    return __all_sync(kFull, gcol || c.idle);
+}
+
+// A lane's vote for extra (fine) work: idle groups never ask for it.
+template <int MODE>
+__device__ __forceinline__ bool wants(const Ctl &c, bool v) {
+    return MODE == kStopGroups ? (v && !c.idle) : v;
 }
 
 // Coarse tests issued per warp vote, per primitive kind (independent
 // dependency chains for the schedulers to interleave).
-#ifndef VP_VOTE_MODE
-#define VP_VOTE_MODE 1  // 0: one REDUX.OR per chunk; 1: one vote, then a vote per primitive
-#endif
 #ifndef VP_UNROLL_SPHERE
 #define VP_UNROLL_SPHERE 8
 #endif
@@ -310,9 +325,9 @@ struct CuboidKind {
 // sphere on U primitives at a time (independent chains, one warp vote per
 // chunk), then fine tests of the link's spheres on each primitive some lane's
 // coarse sphere touched.  Returns the group's stop decision.
-template <class K, int U, bool ANY, bool STATS>
+template <class K, int U, int MODE, bool STATS>
 __device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, const Fr &f, float3 cl, float Rl,
-                                         const float4 *prims, int n, unsigned mask, bool &col,
+                                         const float4 *prims, int n, const Ctl &ctl, bool &col,
                                          const WorkRef<STATS> &w, int fine_counter) {
     for (int o0 = 0; o0 < n; o0 += U) {
         unsigned bits = 0;
@@ -325,15 +340,12 @@ __device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, c
                 bits |= static_cast<unsigned>(K::hit(cl, Rl, ob)) << u;
             }
         }
-#if VP_VOTE_MODE == 0
-        unsigned any = __reduce_or_sync(mask, bits);
-#else
+        if (MODE == kStopGroups && ctl.idle) bits = 0;
         unsigned any = 0;
-        if (__any_sync(mask, bits != 0)) {
+        if (__any_sync(kFull, bits != 0)) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) any |= static_cast<unsigned>(__any_sync(mask, (bits >> u) & 1u)) << u;
+            for (int u = 0; u < U; ++u) any |= static_cast<unsigned>(__any_sync(kFull, (bits >> u) & 1u)) << u;
         }
-#endif
         while (any) {
             const int u = __ffs(any) - 1;
             any &= any - 1;
@@ -346,7 +358,7 @@ __device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, c
                 const float4 sp = P.spheres[s];
                 col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, ob);
             }
-            if (group_stop<ANY>(mask, col)) return true;
+            if (group_stop<MODE>(ctl, col)) return true;
         }
     }
     return false;
@@ -355,9 +367,9 @@ __device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, c
 // Check link l (posed as f) against the environment, coarse then fine, then
 // its self-collision groups.  `col` accumulates this lane's collision; the
 // return value is the group's stop decision.
-template <bool ANY, bool STATS, class QF>
+template <int MODE, bool STATS, class QF>
 __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr &f, float3 &cl, const QF &qf,
-                                           const EnvSm &env, const Stash &stash, unsigned mask, bool &col,
+                                           const EnvSm &env, const Stash &stash, const Ctl &ctl, bool &col,
                                            const WorkRef<STATS> &w) {
     const LinkC &L = P.links[l];
     const bool has_spheres = L.s0 < L.s1;
@@ -368,12 +380,12 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
         w.add(VP_WORK_COARSE_SPHERE, env.ns);
         w.add(VP_WORK_COARSE_CAPSULE, env.nc);
         w.add(VP_WORK_COARSE_CUBOID, env.nb);
-        if (env_pass<SphereKind, VP_UNROLL_SPHERE, ANY, STATS>(P, L, f, cl, Rl, env.sph, env.ns, mask, col, w, VP_WORK_FINE_SPHERE))
+        if (env_pass<SphereKind, VP_UNROLL_SPHERE, MODE, STATS>(P, L, f, cl, Rl, env.sph, env.ns, ctl, col, w, VP_WORK_FINE_SPHERE))
             return true;
-        if (env_pass<CapsuleKind, VP_UNROLL_CAPSULE, ANY, STATS>(P, L, f, cl, Rl, env.cap, env.nc, mask, col, w,
+        if (env_pass<CapsuleKind, VP_UNROLL_CAPSULE, MODE, STATS>(P, L, f, cl, Rl, env.cap, env.nc, ctl, col, w,
                                                   VP_WORK_FINE_CAPSULE))
             return true;
-        if (env_pass<CuboidKind, VP_UNROLL_CUBOID, ANY, STATS>(P, L, f, cl, Rl, env.box, env.nb, mask, col, w,
+        if (env_pass<CuboidKind, VP_UNROLL_CUBOID, MODE, STATS>(P, L, f, cl, Rl, env.box, env.nb, ctl, col, w,
                                                  VP_WORK_FINE_CUBOID))
             return true;
     }
@@ -392,7 +404,7 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
         const float rr = La.bs.w + L.bs.w;
         const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
         w.add(VP_WORK_PAIR_COARSE, 1);
-        if (__any_sync(mask, h)) {
+        if (__any_sync(kFull, wants<MODE>(ctl, h))) {
             Fr fa;
             if (G.slot_a >= 0)
                 recompute_frame(P, G.la, qf, fa);
@@ -410,7 +422,7 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
                 const float r2 = sa.w + sb.w;
                 col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
             }
-            if (group_stop<ANY>(mask, col)) return true;
+            if (group_stop<MODE>(ctl, col)) return true;
         }
     }
     return false;
@@ -419,10 +431,10 @@ __device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr
 // Pose a configuration link by link and check each link as soon as it is
 // posed (Sec. III-D: checks interleaved into FK; links after a collision are
 // never posed).  qf(j) returns joint j's coordinate for this lane.
-// Returns this lane's collision flag (the group stops early per ANY).
-template <bool ANY, bool STATS, class QF>
+// Returns this lane's collision flag (the warp stops early per MODE).
+template <int MODE, bool STATS, class QF>
 __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
-                                               const Stash &stash, unsigned mask, const WorkRef<STATS> &w) {
+                                               const Stash &stash, const Ctl &ctl, const WorkRef<STATS> &w) {
     bool col = false;
     Fr f;
     fr_identity(f);
@@ -441,7 +453,7 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
                 stash.load_frame(pm, f);
             apply_joint(J, qf(l - 1), f);
         }
-        if (check_link<ANY, STATS>(P, l, f, cl, qf, env, stash, mask, col, w)) return col;
+        if (check_link<MODE, STATS>(P, l, f, cl, qf, env, stash, ctl, col, w)) return col;
         const LinkC &Lk = P.links[l];
         if (Lk.slot >= 0) stash.store_frame(Lk.slot, f);
         if (Lk.cslot >= 0) stash.store_centre(Lk.cslot, cl);

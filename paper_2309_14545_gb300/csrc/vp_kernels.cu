@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
                 if (!real) i = k - 1;
                 const float t = static_cast<float>(i) * inv;
                 const WorkRef<STATS> w{&wk, real};
-                const bool c = pose_and_check<true, STATS>(
-                    P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, kFull, w);
+                const bool c = pose_and_check<kStopAny, STATS>(
+                    P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, Ctl{kFull, false}, w);
                 if (__any_sync(kFull, c)) {
                     collided = true;
                     break;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ Rob
         bool fin = true;
         for (int j = 0; j < D; ++j) fin &= isfinite(qi[j]);
         const WorkRef<false> w{nullptr, false};
-        const bool c = pose_and_check<false, false>(P, [qi](int j) { return qi[j]; }, es, stash, kFull, w);
+        const bool c = pose_and_check<kStopAll, false>(P, [qi](int j) { return qi[j]; }, es, stash, Ctl{kFull, false}, w);
         if (real) valid[i] = (c || !fin) ? 0 : 1;
     }
 }

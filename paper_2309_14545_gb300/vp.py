@@ -69,7 +69,7 @@ def _load_lib():
         "vp_validate_states": (U, [P, P, I64, P, P]),
         "vp_edge_counts": (U, [P, P, P, F, I64, P, P]),
         "vp_validate_edges": (U, [P, P, P, P, F, I64, P, U, P]),
-        "vp_validate_edges_work": (U, [P, P, P, P, F, I64, P, P, P]),
+        "vp_validate_edges_work": (U, [P, P, P, P, F, I64, P, U, P, P]),
         "vp_collision_cost": (U, [P, P, I64, F, P, P, P]),
         "vp_autotune": (U, [P, P, P, P, F, I64, P]),
         "vp_sync_status": (U, [P, P, C.POINTER(C.c_uint32)]),
@@ -194,12 +194,12 @@ def vp_validate_edges(ctx, q0, q1, counts, resolution, valid, mode=VP_MODE_PLAIN
                                       _dev(valid, torch.uint8, "valid", (E,)), int(mode), _stream(stream)))
 
 
-def vp_validate_edges_work(ctx, q0, q1, counts, resolution, valid, work, stream=None):
+def vp_validate_edges_work(ctx, q0, q1, counts, resolution, valid, mode, work, stream=None):
     E = q0.shape[0]
     _check(ctx, lib.vp_validate_edges_work(ctx, _dev(q0, torch.float32, "q0"),
                                            _dev(q1, torch.float32, "q1", q0.shape),
                                            _dev(counts, torch.int32, "counts", (E,)), C.c_float(resolution), E,
-                                           _dev(valid, torch.uint8, "valid", (E,)),
+                                           _dev(valid, torch.uint8, "valid", (E,)), int(mode),
                                            _dev(work, torch.int64, "work", (VP_WORK_N,)), _stream(stream)))
 
 

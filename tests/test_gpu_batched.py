@@ -1,0 +1,116 @@
+"""Batched mode (length-bucketed persistent kernel replayed from a CUDA
+graph, tiling from the autotuner) against the plain kernel and the oracle.
+
+Verdicts of the two modes must agree bit for bit on every edge (same
+arithmetic, only the lane assignment differs), and pinned edges must agree
+with the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import vpgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vpmod(cuda_ok):
+    from paper_2309_14545_gb300 import build
+    build.build()
+    from paper_2309_14545_gb300 import Validator, vp
+    return Validator, vp
+
+
+def _cuda(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _both(val, vp, w, tune):
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    plain = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    if tune:
+        val.autotune(q0, q1, c, float(w.res))
+    out = torch.full((w.q0.shape[0],), 9, dtype=torch.uint8, device="cuda")
+    val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
+    first = out.cpu().numpy()
+    out.fill_(9)
+    val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)  # graph replay
+    assert val.sync_status()[0] == vp.VP_OK
+    return plain, first, out.cpu().numpy()
+
+
+@pytest.mark.parametrize("cfg,n,tune", [(0, None, False), (0, None, True), (2, None, True), (4, 300_000, True),
+                                        (1, 200_000, True)])
+def test_batched_equals_plain(vpmod, cfg, n, tune):
+    Validator, vp = vpmod
+    w = vpgen.workload(cfg, n_edges=n)
+    val = Validator(w.robot, w.env)
+    plain, b1, b2 = _both(val, vp, w, tune)
+    assert np.array_equal(plain, b1) and np.array_equal(plain, b2)
+    val.close()
+
+
+def test_batched_mixed_lengths_against_oracle(vpmod):
+    """Every length bucket (2 .. 1000 states) in one batch, ragged size,
+    explicit counts; pinned edges match the oracle."""
+    Validator, vp = vpmod
+    w = vpgen.workload(0, n_edges=3001)
+    rng = np.random.default_rng(9)
+    counts = rng.choice([2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 64, 65, 200, 256, 257, 512, 700, 1000],
+                        size=3001).astype(np.int32)
+    val = Validator(w.robot, w.env)
+    q0, q1 = _cuda(w.q0), _cuda(w.q1)
+    val.autotune(q0, q1, _cuda(counts), float(w.res))
+    got = val.validate_edges(q0, q1, _cuda(counts), float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+    plain = val.validate_edges(q0, q1, _cuda(counts), float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    assert np.array_equal(got, plain)
+    cls, _ = oracle.Oracle(w.robot, w.env).classify_edges(w.q0, w.q1, counts, w.res)
+    pinned = cls != 2
+    assert np.array_equal(got[pinned], (cls[pinned] == 0).astype(np.uint8))
+    assert 0 < got.mean() < 1
+
+
+def test_batched_edge_cases(vpmod):
+    """Bad counts and non-finite endpoints are answered in the bucketing
+    pass (invalid + device status); tiny and empty batches; new buffers
+    after a graph was built."""
+    Validator, vp = vpmod
+    w = vpgen.workload(2, n_edges=70)
+    val = Validator(w.robot, w.env)
+    counts = w.counts.copy()
+    counts[3] = 0
+    q0 = w.q0.copy()
+    q0[5, 2] = np.nan
+    got = val.validate_edges(_cuda(q0), _cuda(w.q1), _cuda(counts), float(w.res), mode=vp.VP_MODE_BATCHED)
+    st, bits = val.sync_status()
+    assert st == vp.VP_ERR_DEVICE and bits & vp.VP_DEVERR_COUNT
+    got = got.cpu().numpy()
+    assert got[3] == 0 and got[5] == 0
+    plain = val.validate_edges(_cuda(q0), _cuda(w.q1), _cuda(counts), float(w.res)).cpu().numpy()
+    val.sync_status()
+    assert np.array_equal(got, plain)
+    for n in (1, 2, 33):
+        a = val.validate_edges(_cuda(w.q0[:n]), _cuda(w.q1[:n]), _cuda(w.counts[:n]), float(w.res),
+                               mode=vp.VP_MODE_BATCHED).cpu().numpy()
+        b = val.validate_edges(_cuda(w.q0[:n]), _cuda(w.q1[:n]), _cuda(w.counts[:n]), float(w.res)).cpu().numpy()
+        assert np.array_equal(a, b)
+    e = torch.zeros((0, 14), device="cuda")
+    assert val.validate_edges(e, e, None, float(w.res), mode=vp.VP_MODE_BATCHED).numel() == 0
+    assert val.sync_status()[0] == vp.VP_OK
+
+
+def test_batched_work_counters(vpmod):
+    """The counting variant of the batched kernel gives the same verdicts and
+    finishes every edge exactly once."""
+    Validator, vp = vpmod
+    w = vpgen.workload(2, n_edges=20_000)
+    val = Validator(w.robot, w.env)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    plain = val.validate_edges(q0, q1, c, float(w.res)).cpu().numpy()
+    got, work = val.validate_edges_work(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED)
+    work = work.cpu().numpy()
+    assert np.array_equal(got.cpu().numpy(), plain)
+    assert work[vp.VP_WORK_EDGES_DONE] == 20_000
+    assert work[vp.VP_WORK_STATES] >= 20_000 * 2 * 0  # at least one state per edge that is posed
+    assert work[vp.VP_WORK_STATES] <= int(w.counts.astype(np.int64).sum())
