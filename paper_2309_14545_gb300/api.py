@@ -99,3 +99,41 @@ class CollisionCost(torch.autograd.Function):
     def backward(ctx, dcost):
         (grad,) = ctx.saved_tensors
         return grad * dcost[:, None], None, None
+
+
+def path_validity(validator: Validator, paths, resolution=1.0 / 32.0, mode=vp.VP_MODE_BATCHED):
+    """Boolean check of waypoint paths [P, W, D]: path p is valid iff all of
+    its W-1 consecutive edges are valid at `resolution`."""
+    P, W, D = paths.shape
+    q0 = paths[:, :-1].reshape(-1, D).contiguous()
+    q1 = paths[:, 1:].reshape(-1, D).contiguous()
+    ok = validator.validate_edges(q0, q1, None, resolution, mode=mode)
+    return ok.view(P, W - 1).bool().all(dim=1)
+
+
+def repair_paths(validator: Validator, paths, margin=0.02, iters=100, lr=0.01, smooth=1.0,
+                 resolution=1.0 / 32.0):
+    """Push the interior waypoints of paths [P, W, D] out of collision by Adam
+    on  sum_i c(q_i) + smooth * sum_i |q_{i+1} - 2 q_i + q_{i-1}|^2  (the
+    cost and its gradient from the FK adjoint kernel; endpoints fixed), then
+    re-judge every path with the boolean edge check.  A path the check
+    accepted before and rejects after repair is kept as it was.
+
+    Returns (paths, valid before [P], valid after [P]); the verdicts always
+    come from the boolean check, never from the cost."""
+    P, W, D = paths.shape
+    before = path_validity(validator, paths, resolution)
+    inner = paths[:, 1:-1].clone().requires_grad_(True)
+    opt = torch.optim.Adam([inner], lr=lr)
+    for _ in range(iters):
+        opt.zero_grad()
+        full = torch.cat([paths[:, :1], inner, paths[:, -1:]], dim=1)
+        c = CollisionCost.apply(inner.reshape(-1, D), validator, margin).sum()
+        acc = full[:, 2:] - 2 * full[:, 1:-1] + full[:, :-2]
+        (c + smooth * (acc * acc).sum()).backward()
+        opt.step()
+    fixed = torch.cat([paths[:, :1], inner.detach(), paths[:, -1:]], dim=1).contiguous()
+    ok_fixed = path_validity(validator, fixed, resolution)
+    take = ok_fixed | ~before
+    out = torch.where(take[:, None, None], fixed, paths).contiguous()
+    return out, before, path_validity(validator, out, resolution)

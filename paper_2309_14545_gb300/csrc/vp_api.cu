@@ -311,6 +311,7 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         const int pl = parent_link[j];
         const int src = (pl == j) ? kParentPrev : (pl == 0 ? kParentBase : slot_of[pl]);
         rp.joints[j].meta |= (src & 0xFF) << kMetaParentShift;
+        rp.joints[j].meta |= (pl & 0xFF) << kMetaParentLinkShift;
     }
     rp.n_groups = ng;
     rp.n_slots = n_slots;

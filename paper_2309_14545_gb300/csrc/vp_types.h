@@ -29,6 +29,7 @@ constexpr int kMetaParentShift = 8;  // 8 bits: parent frame source
 constexpr int kParentPrev = 0xFF;    // the previous joint's link (kept in registers)
 constexpr int kParentBase = 0xFE;    // the base (identity)
 // any other value: the frame-stash slot holding the parent link's frame
+constexpr int kMetaParentLinkShift = 16;  // 8 bits: the parent link's index
 
 // GroupC::slot_a: the centre-stash slot of the earlier link, or
 constexpr int kSlotSameLink = -1;  // both spheres on the current link

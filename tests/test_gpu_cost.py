@@ -1,0 +1,129 @@
+"""Penetration cost and its reverse-mode FK adjoint against the FP64 oracle.
+
+Bars: cost within rtol 1e-4 (+1e-6 absolute); gradient within 1e-3 of the
+oracle's analytic gradient relative to the sample's largest component, plus
+an absolute floor of 5e-5 that covers float32 rounding of positions (about
+1e-6 m) times a lever arm of a metre or two over a few dozen active terms.
+Samples within reach of a kink of the distance (the oracle's central
+differences at h and 2h disagree) are skipped and counted."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import vpgen
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 0.02
+
+
+@pytest.fixture(scope="module")
+def vpmod(cuda_ok):
+    from paper_2309_14545_gb300 import build
+    build.build()
+    from paper_2309_14545_gb300 import CollisionCost, Validator, vp
+    return Validator, CollisionCost, vp
+
+
+def _kinky(o, q, margin):
+    """Samples where FD at h and 2h disagree (near a kink)."""
+    D = q.shape[1]
+    bad = np.zeros(q.shape[0], dtype=bool)
+    for h in (1e-6,):
+        fd = []
+        for hh in (h, 2 * h):
+            Q = np.repeat(q[:, None, :], 2 * D, axis=1)
+            for j in range(D):
+                Q[:, 2 * j, j] += hh
+                Q[:, 2 * j + 1, j] -= hh
+            c = o.cost(Q.reshape(-1, D), margin, grad=False).reshape(-1, 2 * D)
+            fd.append((c[:, 0::2] - c[:, 1::2]) / (2 * hh))
+        scale = np.maximum(1.0, np.abs(fd[0]).max(axis=1))
+        bad |= np.abs(fd[0] - fd[1]).max(axis=1) > 1e-6 * scale
+    return bad
+
+
+def _check(val, o, q, margin):
+    c_gpu, g_gpu = val.collision_cost(torch.from_numpy(q).cuda(), margin, grad=True)
+    c_gpu, g_gpu = c_gpu.cpu().numpy().astype(np.float64), g_gpu.cpu().numpy().astype(np.float64)
+    c_ref, g_ref = o.cost(q.astype(np.float64), margin)
+    np.testing.assert_allclose(c_gpu, c_ref, rtol=1e-4, atol=1e-6)
+    kink = _kinky(o, q.astype(np.float64), margin)
+    ok = ~kink
+    scale = np.abs(g_ref).max(axis=1, keepdims=True)
+    err = np.abs(g_gpu - g_ref)
+    assert np.all(err[ok] <= 1e-3 * scale[ok] + 5e-5), float((err - 1e-3 * scale).max())
+    rel = (err.max(axis=1) / np.maximum(scale[:, 0], 1e-12))[ok & (c_ref > 1e-4)]
+    return kink.mean(), rel
+
+
+def test_cost_and_gradient_config3(vpmod):
+    Validator, _, _ = vpmod
+    w = vpgen.workload(3, n_edges=2048)
+    val = Validator(w.robot, w.env)
+    o = oracle.Oracle(w.robot, w.env)
+    kink_frac, rel = _check(val, o, w.q0, MARGIN)
+    assert kink_frac < 0.05
+    assert (rel <= 1e-3).mean() > 0.95  # the pure relative bar holds on samples with real penetration
+
+
+def test_gradient_tree_prismatic_general_axes(vpmod):
+    """A branching robot with prismatic joints and general axes and origins
+    exercises the subtree accumulation of the reverse sweep."""
+    from robots_small import random_chain
+    Validator, _, _ = vpmod
+    rng = np.random.default_rng(12)
+    r = random_chain(rng, D=9, n_spheres=40)
+    r.joint_parent = np.array([-1, 0, 1, 2, 1, 4, -1, 6, 3], dtype=np.int32)
+    env = vpgen.Env(np.array([[0.1, 0.1, 0.2, 0.3], [-0.2, 0.3, 0.0, 0.25]]),
+                    np.array([[0.0, -0.3, 0.0, 0.3, 0.3, 0.3, 0.1]]),
+                    np.array([np.concatenate([[0.2, 0.0, -0.1], np.eye(3).ravel(), [0.2, 0.15, 0.1]])]))
+    val = Validator(r, env)
+    o = oracle.Oracle(r, env)
+    q = rng.uniform(-1.5, 1.5, size=(1024, 9)).astype(np.float32)
+    kink_frac, rel = _check(val, o, q, MARGIN)
+    assert kink_frac < 0.1
+
+
+def test_cost_zero_and_no_grad(vpmod):
+    Validator, _, _ = vpmod
+    w = vpgen.workload(0, n_edges=8)
+    far = vpgen.Env(np.array([[50.0, 50, 50, 0.1]]), np.zeros((0, 7)), np.zeros((0, 15)))
+    val = Validator(w.robot, far)
+    c, g = val.collision_cost(torch.from_numpy(w.q0).cuda(), MARGIN, grad=True)
+    assert float(c.abs().max()) == 0.0 and float(g.abs().max()) == 0.0
+    c_only = val.collision_cost(torch.from_numpy(w.q0).cuda(), MARGIN, grad=False)
+    assert c_only.shape == (8,)
+
+
+def test_autograd_function(vpmod):
+    Validator, CollisionCost, _ = vpmod
+    w = vpgen.workload(3, n_edges=512)
+    val = Validator(w.robot, w.env)
+    q = torch.from_numpy(w.q0).cuda().requires_grad_(True)
+    weights = torch.linspace(0.5, 1.5, 512, device="cuda")
+    loss = (CollisionCost.apply(q, val, MARGIN) * weights).sum()
+    loss.backward()
+    _, g = val.collision_cost(q.detach(), MARGIN, grad=True)
+    torch.testing.assert_close(q.grad, g * weights[:, None])
+
+
+def test_path_repair_is_rejudged_by_the_boolean_check(vpmod):
+    """Repair lowers the summed penetration cost of the waypoints, and the
+    verdict of every repaired path comes from the boolean edge check (never
+    from the cost): it equals an independent plain-mode check of its edges."""
+    from paper_2309_14545_gb300.api import path_validity, repair_paths
+    Validator, _, vp = vpmod
+    r = vpgen.robot_for(3)
+    env = vpgen.env_for(3)
+    val = Validator(r, env)
+    paths = torch.from_numpy(vpgen.straight_paths(r, 256, 64, seed=303)).cuda()
+    inner = lambda p: p[:, 1:-1].reshape(-1, r.dof).contiguous()  # noqa: E731
+    c0 = val.collision_cost(inner(paths), MARGIN).sum().item()
+    fixed, before, after = repair_paths(val, paths, margin=MARGIN, iters=60, lr=0.02)
+    c1 = val.collision_cost(inner(fixed), MARGIN).sum().item()
+    assert c1 < 0.7 * c0
+    assert torch.equal(after, path_validity(val, fixed, mode=vp.VP_MODE_PLAIN))
+    assert torch.equal(fixed[:, 0], paths[:, 0]) and torch.equal(fixed[:, -1], paths[:, -1])
+    assert bool((after | ~before).all()) and after.sum() >= before.sum()
