@@ -184,8 +184,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--edges", type=int, default=None, help="override the workload's edge count")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--mode", default="batched", choices=["plain", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain/batched/per-edge and grads legs")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     return ap.parse_args()
 
@@ -203,6 +204,34 @@ def config_block(w, args, world):
             "self_pairs": int(len(w.robot.self_pairs)), "primitives": w.env.n_prims,
             "resolution": float(w.res), "explicit_counts": w.counts is not None,
             "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas x{world}"}
+
+
+def rank_workload(cfg, n_edges, rank):
+    """The batch rank `rank` validates: the same robot and scene on every
+    rank, its own seeded edges of the same size (replicas, weak scaling;
+    rank 0 holds the canonical workload)."""
+    base = vpgen.workload(cfg, n_edges=n_edges)
+    if rank == 0:
+        return base
+    seed = 200 + cfg + 1000 * rank
+    q0, q1 = vpgen.uniform_edges(base.robot, base.q0.shape[0], seed=seed)
+    counts = None if base.counts is None else vpgen.loguniform_counts(base.q0.shape[0], seed)
+    return vpgen.Workload(base.name, base.robot, base.env, q0, q1, counts, base.res)
+
+
+def reduce_over_ranks(maxima, sums, device):
+    """Max over ranks of `maxima` (times) and sum of `sums` (work counts);
+    identity without an initialised process group.  The only collective of
+    the run: there is no exchange on the data path."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in maxima], [float(x) for x in sums]
+    t = torch.tensor(list(maxima), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(sums), dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return [float(x) for x in t.cpu()], [float(x) for x in c.cpu()]
 
 
 def run_reference(args):
@@ -238,14 +267,7 @@ def run_native(args):
     torch.cuda.set_device(dev)
     from paper_2309_14545_gb300 import Validator, vp
 
-    # each rank validates its own seeded batch of the same size (weak scaling)
-    base = vpgen.workload(args.config, n_edges=args.edges)
-    if world > 1 and rank > 0:
-        q0, q1 = vpgen.uniform_edges(base.robot, base.q0.shape[0], seed=200 + args.config + 1000 * rank)
-        counts = None if base.counts is None else vpgen.loguniform_counts(base.q0.shape[0], 200 + args.config + 1000 * rank)
-        w = vpgen.Workload(base.name, base.robot, base.env, q0, q1, counts, base.res)
-    else:
-        w = base
+    w = rank_workload(args.config, args.edges, rank)
     E = w.q0.shape[0]
     val = Validator(w.robot, w.env, device=local)
     stream = torch.cuda.Stream(device=dev)
@@ -282,7 +304,8 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    evs = []
+    val.kernel_time(True)
+    ms, kernel_ms = [], []
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             flush.zero_()
@@ -291,10 +314,13 @@ def run_native(args):
             a.record(stream)
             step(valid)
             b.record(stream)
-            evs.append((a, b))
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            kernel_ms.append(val.kernel_time(True))
+    val.kernel_time(False)
     torch.cuda.synchronize(dev)
-    ms = [a.elapsed_time(b) for a, b in evs]
     ms_step = float(np.mean(ms))
+    kms = float(np.mean(kernel_ms))
 
     # e2e: pinned host buffers, copies inside the timed region
     hq0 = torch.from_numpy(w.q0).pin_memory()
@@ -327,18 +353,8 @@ def run_native(args):
     if st != vp.VP_OK:
         raise RuntimeError(f"device status {st} bits {bits:#x}")
 
-    t_max = ms_step
     e2e_step = float(np.mean(e2e_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step, e2e_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max, e2e_step = float(t[0]), float(t[1])
-        c = torch.tensor([covered, float(E)], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        covered_all, edges_all = float(c[0]), float(c[1])
-    else:
-        covered_all, edges_all = covered, float(E)
+    (t_max, e2e_step), (covered_all, edges_all) = reduce_over_ranks([ms_step, e2e_step], [covered, float(E)], dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -349,20 +365,21 @@ def run_native(args):
     n_sm = props.multi_processor_count
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = 2 * 128 * n_sm * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
-    achieved = flops / (ms_step / 1000.0) / 1e12
+    achieved = flops / (kms / 1000.0) / 1e12
     valid_frac = float(valid.float().mean().item())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_block(w, args, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": _traffic(args, E),
+                     "frac": achieved / peak, "traffic": _traffic(args, E, mode),
+                     "kernel_ms": kms,
                      "peak_basis": f"FP32 FMA: 128 lanes x 2 flops x {n_sm} SMs x {sm_max:.0f} MHz (derived)",
                      "kernel": "edges_plain_kernel" if mode == vp.VP_MODE_PLAIN else "edges_batched_kernel",
                      "flops_per_step": flops},
         "e2e": {"value": covered_all / (e2e_step / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
-        "gpu_launches": args.steps * 1,
+        "gpu_launches": args.steps * (3 if mode == vp.VP_MODE_BATCHED else 1),
         "clocks": clocks,
         "extra": {"mode": args.mode, "edges_per_s": edges_all / (t_max / 1000.0),
                   "evaluated_states_per_s": world * int(work[vp.VP_WORK_STATES]) / (t_max / 1000.0),
@@ -370,6 +387,9 @@ def run_native(args):
                   "work_per_step": {n: int(work[i]) for i, n in enumerate(WORK_NAMES)},
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
+    if not args.no_compare:
+        line["comparisons"] = compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev)
+        line["grads"] = grads_leg(dev, flush, stream)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -379,7 +399,94 @@ def run_native(args):
     return 0
 
 
-def _traffic(args, E):
+def _timed(fn, flush, stream, reps):
+    """Median and min ms of fn() over reps runs, L2 flushed before each."""
+    import torch
+    out = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+    return float(np.median(out)), float(np.min(out))
+
+
+def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
+    """Plain single launch vs batched on the headline workload, and on the
+    dual-arm workloads (shelves: also one plain launch per edge; 1,000
+    primitives: 4,194,304 edges).  Verdicts must be identical across modes."""
+    import torch
+    from paper_2309_14545_gb300 import Validator, vp
+    res = {}
+
+    def leg(v, a, b, c, rr, n_edges, reps, per_edge=False):
+        out_p = torch.empty(n_edges, dtype=torch.uint8, device=dev)
+        out_b = torch.empty_like(out_p)
+        v.autotune(a, b, c, rr, stream=stream)
+        plain = _timed(lambda: v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_PLAIN, stream=stream, out=out_p),
+                       flush, stream, reps)
+        batched = _timed(lambda: v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream, out=out_b),
+                         flush, stream, reps + 1)
+        k = c if c is not None else v.edge_counts(a, b, rr, stream=stream)
+        covered = float(k.to(torch.int64).clamp(min=0).sum().item())
+        d = {"edges": n_edges, "covered_states": covered,
+             "plain_ms": plain[0], "batched_ms": batched[0], "batched_vs_plain": plain[0] / batched[0],
+             "batched_states_per_s": covered / (batched[0] / 1e3), "plain_states_per_s": covered / (plain[0] / 1e3),
+             "verdicts_identical": bool(torch.equal(out_p, out_b)),
+             "valid_edge_fraction": float(out_b.float().mean().item())}
+        if per_edge:
+            out_e = torch.empty_like(out_p)
+            pe = _timed(lambda: v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_PER_EDGE, stream=stream, out=out_e),
+                        flush, stream, 1)
+            d["per_edge_launches_ms"] = pe[0]
+            d["batched_vs_per_edge"] = pe[0] / batched[0]
+            d["verdicts_identical"] = d["verdicts_identical"] and bool(torch.equal(out_e, out_b))
+        st, bits = v.sync_status(stream)
+        d["device_status"] = int(st)
+        return d
+
+    res[w.name] = leg(val, q0, q1, counts, float(w.res), q0.shape[0], 3)
+    for cfg, per_edge in ((2, True), (4, False)):
+        wc = vpgen.workload(cfg)
+        vc = Validator(wc.robot, wc.env, device=dev.index)
+        with torch.cuda.stream(stream):
+            a = torch.from_numpy(wc.q0).to(dev)
+            b = torch.from_numpy(wc.q1).to(dev)
+            c = torch.from_numpy(wc.counts).to(dev)
+        res[wc.name] = leg(vc, a, b, c, float(wc.res), a.shape[0], 2, per_edge=per_edge)
+        vc.close()
+        del a, b, c
+    return res
+
+
+def grads_leg(dev, flush, stream):
+    """Penetration cost + adjoint gradient on the mixed-primitive scene:
+    65,536 random configurations and 4,096 paths of 64 waypoints."""
+    import torch
+    from paper_2309_14545_gb300 import Validator
+    w = vpgen.workload(3)
+    v = Validator(w.robot, w.env, device=dev.index)
+    out = {}
+    paths = vpgen.straight_paths(w.robot, 4096, 64, seed=303).reshape(-1, w.robot.dof)
+    for name, qh in (("configs", w.q0), ("waypoints", paths)):
+        with torch.cuda.stream(stream):
+            q = torch.from_numpy(np.ascontiguousarray(qh)).to(dev)
+        cost = torch.empty(q.shape[0], dtype=torch.float32, device=dev)
+        grad = torch.empty_like(q)
+        from paper_2309_14545_gb300 import vp
+        med, mn = _timed(lambda: vp.vp_collision_cost(v.ctx, q, w.margin, cost, grad, stream), flush, stream, 5)
+        out[name] = {"n": int(q.shape[0]), "ms": med, "grads_per_s": q.shape[0] / (med / 1e3),
+                     "mean_cost": float(cost.mean().item())}
+    v.close()
+    return out
+
+
+def _traffic(args, E, mode):
     """DRAM bytes per launch from the committed ncu summary, only if it was
     taken on the current kernel sources (else null)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -390,7 +497,7 @@ def _traffic(args, E):
         from paper_2309_14545_gb300 import build
         if rec.get("sources_hash") != build.sources_hash():
             return None
-        ent = rec.get(f"config{args.config}")
+        ent = rec.get(f"config{args.config}-{'batched' if mode == 1 else 'plain'}")
         if not ent:
             return None
         return float(ent["dram_bytes_per_launch"]) * E / float(ent["edges"])

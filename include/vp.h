@@ -212,6 +212,20 @@ vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin
 vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                       float resolution, int64_t n_edges, void *stream);
 
+/* Kernel timing for profiling: enable != 0 makes later vp_validate_edges
+ * calls record CUDA events around their main validation kernel (inside the
+ * replayed graph in VP_MODE_BATCHED); enable == 0 stops it.  If last_ms is
+ * not NULL it receives the duration of that kernel in the most recent timed
+ * call (waits for it to finish), or -1 if there is none. */
+vp_status vp_kernel_time(vp_ctx *ctx, int enable, float *last_ms);
+
+/* Time budget of the batched mode's persistent kernel per launch (seconds,
+ * default 60).  Past it the kernel stops taking work, sets VP_DEVERR_TIMEOUT
+ * and returns; edges it did not reach keep their previous output.  0 makes
+ * the kernel give up at once (a way to exercise the path).  Negative or
+ * non-finite values: VP_ERR_ARG. */
+vp_status vp_set_watchdog(vp_ctx *ctx, double seconds);
+
 /* Synchronise `stream`, read and clear the device status word: VP_OK,
  * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are
  * returned in *bits when bits != NULL. */

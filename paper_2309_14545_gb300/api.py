@@ -82,6 +82,11 @@ class Validator:
     def sync_status(self, stream=None):
         return vp.vp_sync_status(self.ctx, stream)
 
+    def kernel_time(self, enable=True):
+        """Enable/disable timing of the validation kernel; returns the last
+        timed call's kernel milliseconds (-1 if none)."""
+        return vp.vp_kernel_time(self.ctx, enable)
+
 
 class CollisionCost(torch.autograd.Function):
     """c(q) = sum over robot spheres s and primitives o of

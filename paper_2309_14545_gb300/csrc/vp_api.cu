@@ -28,6 +28,9 @@ struct vp_ctx {
     bool env_loaded = false;
     unsigned *status = nullptr;  // device status word
     BatchedState batched;        // scratch and tuned tiling of the batched mode
+    bool timing = false;         // record events around the validation kernel
+    bool timed = false;          // a timed call has been issued
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     std::string err;
 };
 
@@ -115,6 +118,8 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->env_buf) cudaFree(ctx->env_buf);
         if (ctx->status) cudaFree(ctx->status);
         batched_release(ctx->batched);
+        if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+        if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
     }
     delete ctx;
     return VP_OK;
@@ -476,9 +481,15 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     if (!q0 || !q1 || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool timed = ctx->timing && !work && mode != VP_MODE_PER_EDGE;
+    if (timed) ctx->timed = true;
     if (mode == VP_MODE_BATCHED) {
         BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
                       ctx->num_sms, ctx->smem_optin, st};
+        if (timed) {
+            a.ev_start = ctx->ev_start;
+            a.ev_stop = ctx->ev_stop;
+        }
         std::string msg;
         const int rc = work ? batched_work(ctx->batched, a, reinterpret_cast<unsigned long long *>(work), &msg)
                             : batched_validate(ctx->batched, a, &msg);
@@ -503,8 +514,11 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     }
     const int64_t need = (n_edges + wpb - 1) / wpb;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
-    e = launch_edges_plain(ctx->robot, ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
-                           reinterpret_cast<unsigned long long *>(work), static_cast<int>(grid), block, smem, st);
+    if (timed) e = cudaEventRecord(ctx->ev_start, st);
+    if (e == cudaSuccess)
+        e = launch_edges_plain(ctx->robot, ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
+                               reinterpret_cast<unsigned long long *>(work), static_cast<int>(grid), block, smem, st);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(ctx->ev_stop, st);
     return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges");
 }
 
@@ -552,6 +566,34 @@ extern "C" vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, 
     const int rc = batched_autotune(ctx->batched, a, &msg);
     if (rc == 0) return VP_OK;
     return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_autotune: %s", msg.c_str());
+}
+
+extern "C" vp_status vp_kernel_time(vp_ctx *ctx, int enable, float *last_ms) {
+    if (!ctx) return VP_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (enable && !ctx->ev_start) {
+        cudaError_t e = cudaEventCreate(&ctx->ev_start);
+        if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_stop);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_kernel_time");
+    }
+    if (last_ms) {
+        *last_ms = -1.f;
+        if (ctx->timed && ctx->ev_stop) {
+            cudaError_t e = cudaEventSynchronize(ctx->ev_stop);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(last_ms, ctx->ev_start, ctx->ev_stop);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_kernel_time");
+        }
+    }
+    ctx->timing = enable != 0;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_watchdog(vp_ctx *ctx, double seconds) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!(seconds >= 0.0) || !std::isfinite(seconds) || seconds > 1e9)
+        return fail(ctx, VP_ERR_ARG, "watchdog must be a finite number of seconds >= 0");
+    ctx->batched.watchdog_ns = static_cast<unsigned long long>(seconds * 1e9);
+    return VP_OK;
 }
 
 extern "C" vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits) {

@@ -36,12 +36,12 @@ constexpr int kCtrlHist = 0;     // ctrl[0..8]   edges per bucket
 constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
 constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
 constexpr int kCtrlInts = 64;
-constexpr unsigned long long kWatchdogNs = 20ull * 1000 * 1000 * 1000;  // 20 s per launch
 
 struct BatchPlan {
     int G[kNB];            // lanes per edge, per bucket
     int edge_off[kNB + 1]; // bucket b's edges are perm[edge_off[b], edge_off[b+1]) (when !from_hist)
     int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
+    unsigned long long watchdog_ns;  // time budget of one launch
 };
 
 __host__ __device__ __forceinline__ int bucket_of(int k) {
@@ -110,15 +110,15 @@ __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, c
 }
 
 __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restrict__ kbuf,
-                                      int32_t *__restrict__ perm, int *ctrl) {
+                                      int2 *__restrict__ perm, int *ctrl) {
     __shared__ int cnt[kNB], base[kNB], off[kNB + 1];
     if (threadIdx.x == 0) offsets_from_hist(ctrl + kCtrlHist, off);
     if (threadIdx.x < kNB) cnt[threadIdx.x] = 0;
     __syncthreads();
     const long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    int b = -1, r = 0;
+    int b = -1, r = 0, k = 0;
     if (e < E) {
-        const int k = kbuf[e];
+        k = kbuf[e];
         if (k >= 2) {
             b = bucket_of(k);
             r = atomicAdd(&cnt[b], 1);
@@ -128,7 +128,7 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
     if (threadIdx.x < kNB && cnt[threadIdx.x])
         base[threadIdx.x] = atomicAdd(&ctrl[kCtrlCursor + threadIdx.x], cnt[threadIdx.x]);
     __syncthreads();
-    if (b >= 0) perm[off[b] + base[b] + r] = static_cast<int32_t>(e);
+    if (b >= 0) perm[off[b] + base[b] + r] = make_int2(static_cast<int>(e), k);
 }
 
 // Persistent validation of bucketed edges; see the file comment.  STATS adds
@@ -136,8 +136,8 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
 template <bool STATS>
 __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
-    const float *__restrict__ q1, const int32_t *__restrict__ kbuf, const int32_t *__restrict__ perm,
-    const BatchPlan plan, uint8_t *__restrict__ valid, unsigned *status, int *ctrl, unsigned long long *work) {
+    const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
+    unsigned *status, int *ctrl, unsigned long long *work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_edge_lo[kNB], s_edge_hi[kNB], s_item_end[kNB];
     __shared__ int s_items;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
     while (true) {
         int item = 0;
         if (lane == 0) {
-            if (global_ns() - t_start > kWatchdogNs) {
+            if (global_ns() - t_start >= plan.watchdog_ns) {
                 atomicOr(status, VP_DEVERR_TIMEOUT);
                 item = -1;
             } else {
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
         const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
         const int slot = s_edge_lo[b] + (item - first_item) * per + g;
         const bool has_edge = g < per && slot < s_edge_hi[b];
-        const int e = has_edge ? perm[slot] : 0;
-        int k = has_edge ? kbuf[e] : 2;
+        const int2 ek = has_edge ? perm[slot] : make_int2(0, 2);
+        const int e = ek.x, k = ek.y;
         float *gq0 = wbuf + g * 32, *gdq = gq0 + 16;
         __syncwarp();
         if (has_edge) {
@@ -280,13 +280,16 @@ std::mutex g_tune_mutex;
 std::map<TuneKey, std::vector<int>> g_tune_cache;
 
 struct Impl {
-    int32_t *kbuf = nullptr, *perm = nullptr;
+    int32_t *kbuf = nullptr;  // state count per edge (-1: answered in the bucketing pass)
+    int2 *perm = nullptr;     // (edge, count) bucket by bucket, longest bucket first
     int *ctrl = nullptr;
     int64_t cap = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     // graph key
     const void *k_q0 = nullptr, *k_q1 = nullptr, *k_counts = nullptr, *k_valid = nullptr;
+    const void *k_ev = nullptr;
+    unsigned long long k_watchdog = 0;
     int64_t k_E = -1;
     float k_res = 0.f;
     int G[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
@@ -322,11 +325,12 @@ int ensure_capacity(Impl *im, int64_t E, std::string *msg) {
     drop_graph(im);
     if (im->kbuf) cudaFree(im->kbuf);
     if (im->perm) cudaFree(im->perm);
-    im->kbuf = im->perm = nullptr;
+    im->kbuf = nullptr;
+    im->perm = nullptr;
     im->cap = 0;
     const int64_t n = std::max<int64_t>(E, 1 << 16);
     cudaError_t e = cudaMalloc(&im->kbuf, n * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&im->perm, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&im->perm, n * sizeof(int2));
     if (e != cudaSuccess) return set_err(msg, "cudaMalloc scratch", e);
     im->cap = n;
     return 0;
@@ -364,20 +368,26 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_
     const unsigned nb = static_cast<unsigned>((a.E + 255) / 256);
     bucket_count_kernel<<<nb, 256, 0, s>>>(D, a.q0, a.q1, a.counts, a.res, a.E, im->kbuf, valid, a.status, im->ctrl);
     bucket_scatter_kernel<<<nb, 256, 0, s>>>(a.E, im->kbuf, im->perm, im->ctrl);
+    // external event-record nodes, so the events time the kernel when replayed from the graph
+    if (a.ev_start) e = cudaEventRecordWithFlags(a.ev_start, s, cudaEventRecordExternal);
+    if (e != cudaSuccess) return e;
     if (work)
-        edges_batched_kernel<true><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf, im->perm, plan,
-                                                              valid, a.status, im->ctrl, work);
+        edges_batched_kernel<true><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, plan, valid,
+                                                              a.status, im->ctrl, work);
     else
-        edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf, im->perm,
-                                                               plan, valid, a.status, im->ctrl, nullptr);
-    return cudaGetLastError();
+        edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, plan, valid,
+                                                               a.status, im->ctrl, nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && a.ev_stop) e = cudaEventRecordWithFlags(a.ev_stop, s, cudaEventRecordExternal);
+    return e;
 }
 
-BatchPlan plan_from(const Impl *im) {
+BatchPlan plan_from(const Impl *im, unsigned long long watchdog_ns) {
     BatchPlan p;
     std::memset(&p, 0, sizeof(p));
     for (int b = 0; b < kNB; ++b) p.G[b] = im->G[b];
     p.from_hist = 1;
+    p.watchdog_ns = watchdog_ns;
     return p;
 }
 
@@ -392,13 +402,14 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     rc = prepare_kernel(a, &smem, &grid, msg);
     if (rc) return rc;
     const bool same = im->exec && im->k_q0 == a.q0 && im->k_q1 == a.q1 && im->k_counts == a.counts &&
-                      im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res;
+                      im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res && im->k_ev == a.ev_start &&
+                      im->k_watchdog == st.watchdog_ns;
     if (!same) {
         drop_graph(im);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(im->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return set_err(msg, "begin capture", e);
-        cudaError_t e2 = enqueue(im, a, plan_from(im), smem, grid, im->cap_stream, a.valid);
+        cudaError_t e2 = enqueue(im, a, plan_from(im, st.watchdog_ns), smem, grid, im->cap_stream, a.valid);
         e = cudaStreamEndCapture(im->cap_stream, &graph);
         if (e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -417,6 +428,8 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         im->k_valid = a.valid;
         im->k_E = a.E;
         im->k_res = a.res;
+        im->k_ev = a.ev_start;
+        im->k_watchdog = st.watchdog_ns;
     }
     cudaError_t e = cudaGraphLaunch(im->exec, a.stream);
     return e == cudaSuccess ? 0 : set_err(msg, "graph launch", e);
@@ -430,7 +443,7 @@ int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *wor
     int grid = 0;
     rc = prepare_kernel(a, &smem, &grid, msg);
     if (rc) return rc;
-    const cudaError_t e = enqueue(im, a, plan_from(im), smem, grid, a.stream, a.valid, work);
+    const cudaError_t e = enqueue(im, a, plan_from(im, st.watchdog_ns), smem, grid, a.stream, a.valid, work);
     return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
 }
 
@@ -510,13 +523,14 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
             // only bucket b: every other bucket empty
             for (int c = 0; c <= kNB; ++c) p.edge_off[c] = (c <= b) ? off[b] : off[b] + hist[b];
             p.from_hist = 0;
+            p.watchdog_ns = st.watchdog_ns;
             float ms_min = 1e30f;
             for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
                 e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
                 if (e != cudaSuccess) break;
                 cudaEventRecord(t0, s);
-                edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->kbuf,
-                                                                       im->perm, p, tv, a.status, im->ctrl, nullptr);
+                edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, p,
+                                                                       tv, a.status, im->ctrl, nullptr);
                 cudaEventRecord(t1, s);
                 e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaGetLastError();

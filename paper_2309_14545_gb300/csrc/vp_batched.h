@@ -22,10 +22,12 @@ struct BatchedArgs {
     int num_sms;
     size_t smem_optin;
     cudaStream_t stream;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // timing events around the persistent kernel
 };
 
 struct BatchedState {
     void *impl = nullptr;
+    unsigned long long watchdog_ns = 60ull * 1000 * 1000 * 1000;  // persistent kernel time budget
 };
 
 // 0 = ok, 1 = capacity, 2 = CUDA error (message in *msg)

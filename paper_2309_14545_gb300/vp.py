@@ -33,7 +33,8 @@ VP_WORK_N = 16
 #: Every symbol include/vp.h declares.
 EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load_env", "vp_fk_spheres",
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
-           "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc")
+           "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
+           "vp_kernel_time", "vp_set_watchdog")
 
 
 class VPError(RuntimeError):
@@ -74,6 +75,8 @@ def _load_lib():
         "vp_autotune": (U, [P, P, P, P, F, I64, P]),
         "vp_sync_status": (U, [P, P, C.POINTER(C.c_uint32)]),
         "vp_validate_edges_noalloc": (U, [P, P, P, P, P, F, I64, P, P, C.c_char_p, I32]),
+        "vp_kernel_time": (U, [P, U, C.POINTER(C.c_float)]),
+        "vp_set_watchdog": (U, [P, C.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +218,17 @@ def vp_autotune(ctx, q0, q1, counts, resolution, stream=None):
     _check(ctx, lib.vp_autotune(ctx, _dev(q0, torch.float32, "q0"), _dev(q1, torch.float32, "q1", q0.shape),
                                 _dev(counts, torch.int32, "counts", (E,)), C.c_float(resolution), E,
                                 _stream(stream)))
+
+
+def vp_kernel_time(ctx, enable=True):
+    """Enable/disable kernel timing; returns the last timed kernel's ms (-1 if none)."""
+    ms = C.c_float(-1.0)
+    _check(ctx, lib.vp_kernel_time(ctx, int(bool(enable)), C.byref(ms)))
+    return ms.value
+
+
+def vp_set_watchdog(ctx, seconds):
+    _check(ctx, lib.vp_set_watchdog(ctx, C.c_double(seconds)))
 
 
 def vp_sync_status(ctx, stream=None):

@@ -114,3 +114,44 @@ def test_batched_work_counters(vpmod):
     assert work[vp.VP_WORK_EDGES_DONE] == 20_000
     assert work[vp.VP_WORK_STATES] >= 20_000 * 2 * 0  # at least one state per edge that is posed
     assert work[vp.VP_WORK_STATES] <= int(w.counts.astype(np.int64).sum())
+
+
+def test_kernel_timing_hook(vpmod):
+    """vp_kernel_time reports the validation kernel's own duration, for both
+    modes (inside the replayed graph for batched)."""
+    Validator, vp = vpmod
+    w = vpgen.workload(2, n_edges=50_000)
+    val = Validator(w.robot, w.env)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    assert val.kernel_time(True) == -1.0
+    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED, vp.VP_MODE_BATCHED):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        val.validate_edges(q0, q1, c, float(w.res), mode=mode)
+        b.record()
+        b.synchronize()
+        k = val.kernel_time(True)
+        assert 0.0 < k <= a.elapsed_time(b) * 1.05 + 0.01
+    val.kernel_time(False)
+
+
+def test_watchdog_reports_timeout_and_context_survives(vpmod):
+    """A zero time budget makes the persistent kernel give up at once: the
+    device status reports VP_ERR_TIMEOUT (no fault, no hang), and the same
+    context then validates correctly with the budget restored."""
+    Validator, vp = vpmod
+    w = vpgen.workload(2, n_edges=4096)
+    val = Validator(w.robot, w.env)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    vp.vp_set_watchdog(val.ctx, 0.0)
+    val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED)
+    st, bits = val.sync_status()
+    assert st == vp.VP_ERR_TIMEOUT and bits & vp.VP_DEVERR_TIMEOUT
+    vp.vp_set_watchdog(val.ctx, 60.0)
+    got = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+    assert val.sync_status()[0] == vp.VP_OK
+    plain = val.validate_edges(q0, q1, c, float(w.res)).cpu().numpy()
+    assert np.array_equal(got, plain)
+    with pytest.raises(vp.VPError):
+        vp.vp_set_watchdog(val.ctx, -1.0)
