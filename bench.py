@@ -182,7 +182,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--workload", default=vpgen.TORSO8_OBB60_CAP20, choices=list(vpgen.NAMES))
     ap.add_argument("--edges", type=int, default=None, help="override the workload's edge count")
     ap.add_argument("--mode", default="batched", choices=["plain", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -199,21 +199,21 @@ def dist_info():
 
 
 def config_block(w, args, world):
-    return {"workload": vpgen.DESCRIPTION.get(args.config, w.name), "config_index": args.config,
+    return {"workload": vpgen.DESCRIPTION[w.name], "name": w.name,
             "edges_per_gpu": int(w.q0.shape[0]), "dof": w.robot.dof, "spheres": w.robot.n_spheres,
             "self_pairs": int(len(w.robot.self_pairs)), "primitives": w.env.n_prims,
             "resolution": float(w.res), "explicit_counts": w.counts is not None,
             "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas x{world}"}
 
 
-def rank_workload(cfg, n_edges, rank):
+def rank_workload(name, n_edges, rank):
     """The batch rank `rank` validates: the same robot and scene on every
     rank, its own seeded edges of the same size (replicas, weak scaling;
     rank 0 holds the canonical workload)."""
-    base = vpgen.workload(cfg, n_edges=n_edges)
+    base = vpgen.workload(name, n_edges=n_edges)
     if rank == 0:
         return base
-    seed = 200 + cfg + 1000 * rank
+    seed = 200 + vpgen.NAMES.index(name) + 1000 * rank
     q0, q1 = vpgen.uniform_edges(base.robot, base.q0.shape[0], seed=seed)
     counts = None if base.counts is None else vpgen.loguniform_counts(base.q0.shape[0], seed)
     return vpgen.Workload(base.name, base.robot, base.env, q0, q1, counts, base.res)
@@ -238,7 +238,7 @@ def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
         return 0
-    w = vpgen.workload(args.config, n_edges=args.edges)
+    w = vpgen.workload(args.workload, n_edges=args.edges)
     times = []
     rate = None
     for i in range(args.warmup + args.steps):
@@ -267,7 +267,7 @@ def run_native(args):
     torch.cuda.set_device(dev)
     from paper_2309_14545_gb300 import Validator, vp
 
-    w = rank_workload(args.config, args.edges, rank)
+    w = rank_workload(args.workload, args.edges, rank)
     E = w.q0.shape[0]
     val = Validator(w.robot, w.env, device=local)
     stream = torch.cuda.Stream(device=dev)
@@ -451,8 +451,8 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
         return d
 
     res[w.name] = leg(val, q0, q1, counts, float(w.res), q0.shape[0], 3)
-    for cfg, per_edge in ((2, True), (4, False)):
-        wc = vpgen.workload(cfg)
+    for name, per_edge in ((vpgen.DUAL14_SHELVES, True), (vpgen.DUAL14_MIXED1000, False)):
+        wc = vpgen.workload(name)
         vc = Validator(wc.robot, wc.env, device=dev.index)
         with torch.cuda.stream(stream):
             a = torch.from_numpy(wc.q0).to(dev)
@@ -469,7 +469,7 @@ def grads_leg(dev, flush, stream):
     65,536 random configurations and 4,096 paths of 64 waypoints."""
     import torch
     from paper_2309_14545_gb300 import Validator
-    w = vpgen.workload(3)
+    w = vpgen.workload(vpgen.ARM7_MIXED128)
     v = Validator(w.robot, w.env, device=dev.index)
     out = {}
     paths = vpgen.straight_paths(w.robot, 4096, 64, seed=303).reshape(-1, w.robot.dof)
@@ -497,7 +497,7 @@ def _traffic(args, E, mode):
         from paper_2309_14545_gb300 import build
         if rec.get("sources_hash") != build.sources_hash():
             return None
-        ent = rec.get(f"config{args.config}-{'batched' if mode == 1 else 'plain'}")
+        ent = rec.get(f"{args.workload}-{'batched' if mode == 1 else 'plain'}")
         if not ent:
             return None
         return float(ent["dram_bytes_per_launch"]) * E / float(ent["edges"])

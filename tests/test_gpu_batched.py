@@ -40,11 +40,12 @@ def _both(val, vp, w, tune):
     return plain, first, out.cpu().numpy()
 
 
-@pytest.mark.parametrize("cfg,n,tune", [(0, None, False), (0, None, True), (2, None, True), (4, 300_000, True),
-                                        (1, 200_000, True)])
-def test_batched_equals_plain(vpmod, cfg, n, tune):
+@pytest.mark.parametrize("name,n,tune", [(vpgen.ARM7_SPHERES16, None, False), (vpgen.ARM7_SPHERES16, None, True),
+                                         (vpgen.DUAL14_SHELVES, None, True), (vpgen.DUAL14_MIXED1000, 300_000, True),
+                                         (vpgen.TORSO8_OBB60_CAP20, 200_000, True)])
+def test_batched_equals_plain(vpmod, name, n, tune):
     Validator, vp = vpmod
-    w = vpgen.workload(cfg, n_edges=n)
+    w = vpgen.workload(name, n_edges=n)
     val = Validator(w.robot, w.env)
     plain, b1, b2 = _both(val, vp, w, tune)
     assert np.array_equal(plain, b1) and np.array_equal(plain, b2)
@@ -55,7 +56,7 @@ def test_batched_mixed_lengths_against_oracle(vpmod):
     """Every length bucket (2 .. 1000 states) in one batch, ragged size,
     explicit counts; pinned edges match the oracle."""
     Validator, vp = vpmod
-    w = vpgen.workload(0, n_edges=3001)
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=3001)
     rng = np.random.default_rng(9)
     counts = rng.choice([2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33, 64, 65, 200, 256, 257, 512, 700, 1000],
                         size=3001).astype(np.int32)
@@ -76,7 +77,7 @@ def test_batched_edge_cases(vpmod):
     pass (invalid + device status); tiny and empty batches; new buffers
     after a graph was built."""
     Validator, vp = vpmod
-    w = vpgen.workload(2, n_edges=70)
+    w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=70)
     val = Validator(w.robot, w.env)
     counts = w.counts.copy()
     counts[3] = 0
@@ -104,7 +105,7 @@ def test_batched_work_counters(vpmod):
     """The counting variant of the batched kernel gives the same verdicts and
     finishes every edge exactly once."""
     Validator, vp = vpmod
-    w = vpgen.workload(2, n_edges=20_000)
+    w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=20_000)
     val = Validator(w.robot, w.env)
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
     plain = val.validate_edges(q0, q1, c, float(w.res)).cpu().numpy()
@@ -120,7 +121,7 @@ def test_kernel_timing_hook(vpmod):
     """vp_kernel_time reports the validation kernel's own duration, for both
     modes (inside the replayed graph for batched)."""
     Validator, vp = vpmod
-    w = vpgen.workload(2, n_edges=50_000)
+    w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=50_000)
     val = Validator(w.robot, w.env)
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
     assert val.kernel_time(True) == -1.0
@@ -141,7 +142,7 @@ def test_watchdog_reports_timeout_and_context_survives(vpmod):
     device status reports VP_ERR_TIMEOUT (no fault, no hang), and the same
     context then validates correctly with the budget restored."""
     Validator, vp = vpmod
-    w = vpgen.workload(2, n_edges=4096)
+    w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=4096)
     val = Validator(w.robot, w.env)
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
     vp.vp_set_watchdog(val.ctx, 0.0)

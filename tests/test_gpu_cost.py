@@ -58,9 +58,9 @@ def _check(val, o, q, margin):
     return kink.mean(), rel
 
 
-def test_cost_and_gradient_config3(vpmod):
+def test_cost_and_gradient_mixed_scene(vpmod):
     Validator, _, _ = vpmod
-    w = vpgen.workload(3, n_edges=2048)
+    w = vpgen.workload(vpgen.ARM7_MIXED128, n_edges=2048)
     val = Validator(w.robot, w.env)
     o = oracle.Oracle(w.robot, w.env)
     kink_frac, rel = _check(val, o, w.q0, MARGIN)
@@ -88,7 +88,7 @@ def test_gradient_tree_prismatic_general_axes(vpmod):
 
 def test_cost_zero_and_no_grad(vpmod):
     Validator, _, _ = vpmod
-    w = vpgen.workload(0, n_edges=8)
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=8)
     far = vpgen.Env(np.array([[50.0, 50, 50, 0.1]]), np.zeros((0, 7)), np.zeros((0, 15)))
     val = Validator(w.robot, far)
     c, g = val.collision_cost(torch.from_numpy(w.q0).cuda(), MARGIN, grad=True)
@@ -99,7 +99,7 @@ def test_cost_zero_and_no_grad(vpmod):
 
 def test_autograd_function(vpmod):
     Validator, CollisionCost, _ = vpmod
-    w = vpgen.workload(3, n_edges=512)
+    w = vpgen.workload(vpgen.ARM7_MIXED128, n_edges=512)
     val = Validator(w.robot, w.env)
     q = torch.from_numpy(w.q0).cuda().requires_grad_(True)
     weights = torch.linspace(0.5, 1.5, 512, device="cuda")
@@ -115,8 +115,8 @@ def test_path_repair_is_rejudged_by_the_boolean_check(vpmod):
     from the cost): it equals an independent plain-mode check of its edges."""
     from paper_2309_14545_gb300.api import path_validity, repair_paths
     Validator, _, vp = vpmod
-    r = vpgen.robot_for(3)
-    env = vpgen.env_for(3)
+    r = vpgen.robot_for(vpgen.ARM7_MIXED128)
+    env = vpgen.env_for(vpgen.ARM7_MIXED128)
     val = Validator(r, env)
     paths = torch.from_numpy(vpgen.straight_paths(r, 256, 64, seed=303)).cuda()
     inner = lambda p: p[:, 1:-1].reshape(-1, r.dof).contiguous()  # noqa: E731

@@ -29,11 +29,11 @@ def vpmod(cuda_ok):
 _cache = {}
 
 
-def _setup(vpmod, cfg, n_edges):
-    key = (cfg, n_edges)
+def _setup(vpmod, name, n_edges):
+    key = (name, n_edges)
     if key not in _cache:
         Validator, _ = vpmod
-        w = vpgen.workload(cfg, n_edges=n_edges)
+        w = vpgen.workload(name, n_edges=n_edges)
         _cache[key] = (w, Validator(w.robot, w.env), oracle.Oracle(w.robot, w.env))
     return _cache[key]
 
@@ -42,9 +42,9 @@ def _cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2])
-def test_fk_centres(vpmod, cfg):
-    w, val, o = _setup(vpmod, cfg, 64)
+@pytest.mark.parametrize("name", [vpgen.ARM7_SPHERES16, vpgen.TORSO8_OBB60_CAP20, vpgen.DUAL14_SHELVES])
+def test_fk_centres(vpmod, name):
+    w, val, o = _setup(vpmod, name, 64)
     q = vpgen.uniform_configs(w.robot, 4099, seed=31)  # ragged: not a multiple of the block
     got = val.fk_spheres(_cuda(q)).cpu().numpy()
     want = o.fk(q.astype(np.float64))
@@ -68,7 +68,7 @@ def test_fk_general_tree_and_axes(vpmod):
 
 
 def test_edge_counts_bit_exact(vpmod):
-    w, val, o = _setup(vpmod, 0, 4096)
+    w, val, o = _setup(vpmod, vpgen.ARM7_SPHERES16, 4096)
     got = val.edge_counts(_cuda(w.q0), _cuda(w.q1), w.res).cpu().numpy()
     assert np.array_equal(got, o.edge_count(w.q0, w.q1, w.res))
     # hand cases incl. the float32 decision, non-finite and over-long edges
@@ -92,14 +92,15 @@ def _compare_states(val, o, q):
     return got, K, pinned, bad
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
-def test_state_verdicts(vpmod, cfg):
-    w, val, o = _setup(vpmod, cfg, 64)
-    q = vpgen.uniform_configs(w.robot, 3001 if cfg != 4 else 1001, seed=41 + cfg)
+@pytest.mark.parametrize("name", list(vpgen.NAMES))
+def test_state_verdicts(vpmod, name):
+    w, val, o = _setup(vpmod, name, 64)
+    big = name == vpgen.DUAL14_MIXED1000
+    q = vpgen.uniform_configs(w.robot, 1001 if big else 3001, seed=41 + vpgen.NAMES.index(name))
     got, K, pinned, bad = _compare_states(val, o, q)
     assert bad.size == 0, f"{bad.size} pinned states disagree"
     assert pinned.mean() > 0.99
-    assert 0 < got.mean() < 1 or cfg == 4
+    assert 0 < got.mean() < 1 or big
 
 
 def _compare_edges(w, val, o, idx, mode, n_edges=None):
@@ -116,10 +117,11 @@ def _compare_edges(w, val, o, idx, mode, n_edges=None):
     return got, cls, bad
 
 
-def test_edges_config0_every_edge(vpmod):
-    """Config 0 at full size (10,000 edges): every pinned edge matches."""
+def test_edges_arm7_every_edge(vpmod):
+    """The 7-DoF arm workload at full size (10,000 edges): every pinned edge
+    matches."""
     from paper_2309_14545_gb300 import vp
-    w, val, o = _setup(vpmod, 0, None)
+    w, val, o = _setup(vpmod, vpgen.ARM7_SPHERES16, None)
     idx = np.arange(w.q0.shape[0])
     got, cls, bad = _compare_edges(w, val, o, idx, vp.VP_MODE_PLAIN)
     assert bad.size == 0, f"{bad.size} pinned edges disagree"
@@ -127,13 +129,14 @@ def test_edges_config0_every_edge(vpmod):
     assert 0.2 < got.mean() < 0.9
 
 
-@pytest.mark.parametrize("cfg,n_sample", [(1, 768), (2, 512), (4, 256)])
-def test_edges_full_size_sampled(vpmod, cfg, n_sample):
+@pytest.mark.parametrize("name,n_sample", [(vpgen.TORSO8_OBB60_CAP20, 768), (vpgen.DUAL14_SHELVES, 512),
+                                           (vpgen.DUAL14_MIXED1000, 256)])
+def test_edges_full_size_sampled(vpmod, name, n_sample):
     """Full-size workloads in the benchmark's launch configuration, checked
     on a seeded sample of edges the oracle classifies one by one."""
     from paper_2309_14545_gb300 import vp
-    w, val, o = _setup(vpmod, cfg, None)
-    idx = np.sort(np.random.default_rng(cfg).choice(w.q0.shape[0], n_sample, replace=False))
+    w, val, o = _setup(vpmod, name, None)
+    idx = np.sort(np.random.default_rng(n_sample).choice(w.q0.shape[0], n_sample, replace=False))
     got, cls, bad = _compare_edges(w, val, o, idx, vp.VP_MODE_PLAIN)
     assert bad.size == 0, f"{bad.size} pinned edges disagree"
 
@@ -143,7 +146,7 @@ def test_edge_edge_cases(vpmod):
     maximum counts, non-finite endpoints and a count < 2 (reported through
     the device status word, edge invalid)."""
     from paper_2309_14545_gb300 import vp
-    w, val, o = _setup(vpmod, 0, 2000)
+    w, val, o = _setup(vpmod, vpgen.ARM7_SPHERES16, 2000)
     empty = torch.zeros((0, 7), dtype=torch.float32, device="cuda")
     out = val.validate_edges(empty, empty, None, float(w.res))
     assert out.numel() == 0
@@ -172,7 +175,7 @@ def test_edge_edge_cases(vpmod):
 
 def test_per_edge_launches_match_plain(vpmod):
     from paper_2309_14545_gb300 import vp
-    w, val, o = _setup(vpmod, 2, 300)
+    w, val, o = _setup(vpmod, vpgen.DUAL14_SHELVES, 300)
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
     a = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
     b = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PER_EDGE).cpu().numpy()
@@ -181,7 +184,7 @@ def test_per_edge_launches_match_plain(vpmod):
 
 def test_work_counters(vpmod):
     from paper_2309_14545_gb300 import vp
-    w, val, o = _setup(vpmod, 1, 4096)
+    w, val, o = _setup(vpmod, vpgen.TORSO8_OBB60_CAP20, 4096)
     q0, q1 = _cuda(w.q0), _cuda(w.q1)
     a = val.validate_edges(q0, q1, None, float(w.res)).cpu().numpy()
     b, work = val.validate_edges_work(q0, q1, None, float(w.res))
@@ -196,7 +199,7 @@ def test_work_counters(vpmod):
 
 def test_argument_errors(vpmod):
     Validator, vp = vpmod
-    w, val, o = _setup(vpmod, 0, 64)
+    w, val, o = _setup(vpmod, vpgen.ARM7_SPHERES16, 64)
     bad = vpgen.arm7(0, 40)
     bad.joint_parent = np.array([-1, 0, 5, 2, 3, 4, 5], dtype=np.int32)  # parent after child
     with pytest.raises(vp.VPError) as e:

@@ -24,7 +24,8 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = bench.rank_workload(2, 300, rank)
+    import vpgen
+    w = bench.rank_workload(vpgen.DUAL14_SHELVES, 300, rank)
     times = [10.0 + rank, 20.0 - rank]
     sums = [float(w.counts.sum()), 300.0]
     mx, sm = bench.reduce_over_ranks(times, sums, torch.device("cpu"))

@@ -58,7 +58,7 @@ def test_edge_states_endpoints_and_spacing():
 def test_denser_grid_contains_the_grid():
     """States of a k-state edge are every 4th state of the 4(k-1)+1-state
     edge (exactly), so validity at 4x density implies validity at k."""
-    w = vpgen.workload(0, n_edges=300)
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=300)
     o = oracle.Oracle(w.robot, w.env)
     k = o.edge_count(w.q0, w.q1, w.res)
     for e in range(5):
@@ -71,10 +71,10 @@ def test_denser_grid_contains_the_grid():
     assert 0 < v.mean() < 1
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2])
-def test_edge_verdict_is_every_state_valid(cfg):
+@pytest.mark.parametrize("name", [vpgen.ARM7_SPHERES16, vpgen.TORSO8_OBB60_CAP20, vpgen.DUAL14_SHELVES])
+def test_edge_verdict_is_every_state_valid(name):
     """Brute force: the edge verdict equals 'every state has K >= 0'."""
-    w = vpgen.workload(cfg, n_edges=40)
+    w = vpgen.workload(name, n_edges=40)
     o = oracle.Oracle(w.robot, w.env)
     counts = w.counts if w.counts is not None else o.edge_count(w.q0, w.q1, w.res)
     counts = np.minimum(counts, 64)
@@ -94,7 +94,7 @@ def test_edge_verdict_is_every_state_valid(cfg):
 
 
 def test_two_state_and_constant_edges_reduce_to_state_checks():
-    w = vpgen.workload(0, n_edges=200)
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=200)
     o = oracle.Oracle(w.robot, w.env)
     K0 = o.clearance(w.q0.astype(np.float64))
     K1 = o.clearance(w.q1.astype(np.float64))

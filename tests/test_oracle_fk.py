@@ -91,11 +91,11 @@ def test_random_chain_matches_scipy_composition():
             np.testing.assert_allclose(frames[l][:, 3], ts[l], atol=1e-12)
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2])
-def test_frames_orthonormal_and_rigid_links(cfg):
+@pytest.mark.parametrize("name", [vpgen.ARM7_SPHERES16, vpgen.TORSO8_OBB60_CAP20, vpgen.DUAL14_SHELVES])
+def test_frames_orthonormal_and_rigid_links(name):
     """Invariants: every link rotation is orthonormal with det +1, and
     distances between spheres on one link do not depend on q."""
-    r = vpgen.robot_for(cfg)
+    r = vpgen.robot_for(name)
     o = oracle.Oracle(r, EMPTY_ENV)
     q = vpgen.uniform_configs(r, 32, seed=11).astype(np.float64)
     c0 = o.fk(np.zeros((1, r.dof)))[0]

@@ -40,19 +40,20 @@ def _reference(Validator, w):
 
 def test_noalloc_matches_plain_on_consecutive_calls(vpmod):
     Validator, vp = vpmod
-    cases = [vpgen.workload(1, n_edges=20_003), vpgen.workload(0, n_edges=10_000),
-             vpgen.workload(2, n_edges=5_001)]
+    cases = [vpgen.workload(vpgen.TORSO8_OBB60_CAP20, n_edges=20_003),
+             vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=10_000),
+             vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=5_001)]
     for w in cases + cases[:1]:  # the last call follows a different environment
         q0, q1, c, want = _reference(Validator, w)
         got = torch.full((w.q0.shape[0],), 7, dtype=torch.uint8, device="cuda")
         vp.vp_validate_edges_noalloc(w.robot, w.env, q0, q1, c, float(w.res), got)
         assert np.array_equal(got.cpu().numpy(), want), w.name
-        assert 0 < want.mean() < 1 or w.name == "config2"
+        assert 0 < want.mean() < 1 or w.name == vpgen.DUAL14_SHELVES
 
 
 def test_noalloc_rejects_an_environment_beyond_the_scratch(vpmod):
     Validator, vp = vpmod
-    w = vpgen.workload(0, n_edges=64)
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=64)
     n = vp.VP_NOALLOC_MAX_ENV_BYTES // 64 + 1  # cuboids pack to 64 bytes each
     big = vpgen.Env(np.zeros((0, 4)), np.zeros((0, 7)),
                     np.tile(np.concatenate([[5.0, 5, 5], np.eye(3).ravel(), [0.1, 0.1, 0.1]]), (n, 1)))

@@ -489,49 +489,66 @@ def straight_paths(robot: Robot, n_paths: int, n_way: int, seed: int) -> np.ndar
 
 
 # ----------------------------------------------------------------------------
-# the five workloads
+# the five workloads, by name
+
+ARM7_SPHERES16 = "arm7_spheres16"          # 7-DoF arm vs 16 spheres, 10,000 edges
+TORSO8_OBB60_CAP20 = "torso8_obb60_cap20"  # 8-DoF torso arm vs 60 OBBs + 20 capsules, 1,000,000 edges
+DUAL14_SHELVES = "dual14_shelves"          # 14-DoF dual arm vs 120-cuboid shelves, 262,144 edges
+ARM7_MIXED128 = "arm7_mixed128"            # 7-DoF arm vs 128 mixed primitives, 65,536 configurations
+DUAL14_MIXED1000 = "dual14_mixed1000"      # 14-DoF dual arm vs 1,000 mixed primitives, 4,194,304 edges
+NAMES = (ARM7_SPHERES16, TORSO8_OBB60_CAP20, DUAL14_SHELVES, ARM7_MIXED128, DUAL14_MIXED1000)
 
 #: Full sizes of the five workloads.
-FULL_EDGES = {0: 10_000, 1: 1_000_000, 2: 262_144, 3: 65_536, 4: 4_194_304}
+FULL_EDGES = {ARM7_SPHERES16: 10_000, TORSO8_OBB60_CAP20: 1_000_000, DUAL14_SHELVES: 262_144,
+              ARM7_MIXED128: 65_536, DUAL14_MIXED1000: 4_194_304}
 
 DESCRIPTION = {
-    0: "7-DoF arm (40 spheres) vs 16 spheres; 10,000 uniform edges at 1/32 rad",
-    1: "8-DoF torso arm (100 spheres / 9 links / 200 self pairs) vs 60 OBBs + 20 capsules; 1,000,000 edges at 1/32 rad",
-    2: "14-DoF dual arm (120 spheres / 400 self pairs) vs 120-cuboid shelves; 262,144 edges, counts log-uniform in [2,512]",
-    3: "7-DoF arm vs 64 spheres + 32 capsules + 32 OBBs; cost at margin 0.02 on 65,536 configurations",
-    4: "14-DoF dual arm vs 1,000 mixed primitives in a 2 m cube; 4,194,304 edges, counts log-uniform in [2,512]",
+    ARM7_SPHERES16: "7-DoF arm (40 spheres) vs 16 spheres; 10,000 uniform edges at 1/32 rad",
+    TORSO8_OBB60_CAP20: "8-DoF torso arm (100 spheres / 9 links / 200 self pairs) vs 60 OBBs + 20 capsules; "
+                        "1,000,000 edges at 1/32 rad",
+    DUAL14_SHELVES: "14-DoF dual arm (120 spheres / 400 self pairs) vs 120-cuboid shelves; 262,144 edges, "
+                    "counts log-uniform in [2,512]",
+    ARM7_MIXED128: "7-DoF arm vs 64 spheres + 32 capsules + 32 OBBs; cost at margin 0.02 on 65,536 configurations",
+    DUAL14_MIXED1000: "14-DoF dual arm vs 1,000 mixed primitives in a 2 m cube; 4,194,304 edges, counts "
+                      "log-uniform in [2,512]",
 }
 
+# seeds: robots 0/1/2; scenes 100 + index; edges 200 + index (index = position in NAMES)
+_INDEX = {n: i for i, n in enumerate(NAMES)}
 
-def robot_for(cfg: int) -> Robot:
-    if cfg in (0, 3):
+
+def robot_for(name: str) -> Robot:
+    if name in (ARM7_SPHERES16, ARM7_MIXED128):
         return arm7(0, 40)
-    if cfg == 1:
+    if name == TORSO8_OBB60_CAP20:
         return torso_arm8(1, 100, 200)
-    if cfg in (2, 4):
+    if name in (DUAL14_SHELVES, DUAL14_MIXED1000):
         return dual_arm14(60, 400)
-    raise ValueError(cfg)
+    raise ValueError(name)
 
 
-def env_for(cfg: int) -> Env:
-    return {0: env_spheres16, 1: env_boxes_capsules, 2: env_shelves, 3: env_mixed128, 4: env_mixed1000}[cfg]()
+def env_for(name: str) -> Env:
+    return {ARM7_SPHERES16: env_spheres16, TORSO8_OBB60_CAP20: env_boxes_capsules, DUAL14_SHELVES: env_shelves,
+            ARM7_MIXED128: env_mixed128, DUAL14_MIXED1000: env_mixed1000}[name]()
 
 
-def workload(cfg: int, n_edges: Optional[int] = None, robot: Optional[Robot] = None,
+def workload(name: str, n_edges: Optional[int] = None, robot: Optional[Robot] = None,
              env: Optional[Env] = None) -> Workload:
-    """Workload ``cfg`` (0..4) with its first ``n_edges`` edges (default: all).
+    """Workload ``name`` with its first ``n_edges`` edges (default: all).
 
-    Config 3 is a configuration set, returned as ``q0 == q1`` edges of two
-    states (a state check) with ``margin = 0.02``."""
-    robot = robot if robot is not None else robot_for(cfg)
-    env = env if env is not None else env_for(cfg)
-    n = FULL_EDGES[cfg] if n_edges is None else int(n_edges)
-    seed = 200 + cfg
-    if cfg in (0, 1):
+    ``arm7_mixed128`` is a configuration set, returned as ``q0 == q1`` edges
+    with ``margin = 0.02``."""
+    if name not in _INDEX:
+        raise ValueError(f"unknown workload {name!r}; one of {NAMES}")
+    robot = robot if robot is not None else robot_for(name)
+    env = env if env is not None else env_for(name)
+    n = FULL_EDGES[name] if n_edges is None else int(n_edges)
+    seed = 200 + _INDEX[name]
+    if name in (ARM7_SPHERES16, TORSO8_OBB60_CAP20):
         q0, q1 = uniform_edges(robot, n, seed)
-        return Workload(f"config{cfg}", robot, env, q0, q1, None, RESOLUTION)
-    if cfg in (2, 4):
+        return Workload(name, robot, env, q0, q1, None, RESOLUTION)
+    if name in (DUAL14_SHELVES, DUAL14_MIXED1000):
         q0, q1 = uniform_edges(robot, n, seed)
-        return Workload(f"config{cfg}", robot, env, q0, q1, loguniform_counts(n, seed), RESOLUTION)
+        return Workload(name, robot, env, q0, q1, loguniform_counts(n, seed), RESOLUTION)
     q = uniform_configs(robot, n, seed)
-    return Workload("config3", robot, env, q, q.copy(), None, RESOLUTION, margin=0.02)
+    return Workload(name, robot, env, q, q.copy(), None, RESOLUTION, margin=0.02)
