@@ -268,11 +268,11 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     }
     std::stable_sort(prs.begin(), prs.end(),
                      [](const PairRec &x, const PairRec &y) { return x.lb != y.lb ? x.lb < y.lb : x.la < y.la; });
-    // stash slots: centre slots for links that are the earlier member of a
-    // self pair (their frame is recomputed on demand), frame slots for branch
-    // points (a joint whose parent is not the previous joint)
-    std::vector<int> cslot_of(L, -1), slot_of(L, -1);
-    int n_cslots = 0, n_slots = 0;
+    // link-pair groups (the later link lb is where the pair is checked) and
+    // frame-stash slots for branch points (a joint whose parent is not the
+    // previous joint)
+    std::vector<int> slot_of(L, -1);
+    int n_slots = 0;
     int ng = 0;
     for (int i = 0; i < P;) {
         int j = i;
@@ -280,10 +280,9 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         if (ng >= kMaxGroups) return fail(ctx, VP_ERR_CAPACITY, "too many link pairs with self pairs");
         GroupC &G = rp.groups[ng++];
         G.la = static_cast<int16_t>(prs[i].la);
+        G.lb = static_cast<int16_t>(prs[i].lb);
         G.p0 = static_cast<int16_t>(i);
         G.p1 = static_cast<int16_t>(j);
-        const int la = prs[i].la;
-        if (la != prs[i].lb && la > 0 && cslot_of[la] < 0) cslot_of[la] = n_cslots++;
         i = j;
     }
     for (int p = 0; p < P; ++p) rp.pairs[p] = PairC{static_cast<uint16_t>(prs[p].a), static_cast<uint16_t>(prs[p].b)};
@@ -296,18 +295,12 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     for (int j = 0; j < D; ++j) path[j + 1] = path[parent_link[j]] | (1u << j);
     for (int l = 0; l < L; ++l) {
         rp.links[l].slot = static_cast<int16_t>(slot_of[l]);
-        rp.links[l].cslot = static_cast<int16_t>(cslot_of[l]);
         rp.links[l].path = static_cast<uint16_t>(path[l]);
     }
-    for (int g = 0; g < ng; ++g) {
-        GroupC &G = rp.groups[g];
-        const int lb = prs[G.p0].lb;
-        G.slot_a = static_cast<int16_t>(G.la == lb ? kSlotSameLink : (G.la == 0 ? kSlotBase : cslot_of[G.la]));
-    }
     for (int g = 0; g < ng;) {
-        const int lb = prs[rp.groups[g].p0].lb;
+        const int lb = rp.groups[g].lb;
         int h = g;
-        while (h < ng && prs[rp.groups[h].p0].lb == lb) ++h;
+        while (h < ng && rp.groups[h].lb == lb) ++h;
         rp.links[lb].g0 = static_cast<int16_t>(g);
         rp.links[lb].g1 = static_cast<int16_t>(h);
         g = h;
@@ -320,7 +313,14 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     }
     rp.n_groups = ng;
     rp.n_slots = n_slots;
-    rp.n_cslots = n_cslots;
+    rp.link_mask = 0;
+    for (int l = 0; l < L; ++l)
+        if (rp.links[l].s0 < rp.links[l].s1) rp.link_mask |= 1u << l;
+    rp.simple = 1;
+    for (int j = 0; j < D; ++j) {
+        const int m = rp.joints[j].meta;
+        if (!(m & kMetaOriginRotIdentity) || ((m >> kMetaAxisShift) & 3) == kAxisGeneral) rp.simple = 0;
+    }
 
     ctx->robot = rp;
     ctx->sorted_of = sorted_of;
@@ -335,41 +335,14 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
 extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
     if (!ctx) return VP_ERR_ARG;
     if (!e) return fail(ctx, VP_ERR_ARG, "environment descriptor is NULL");
-    const int ns = e->n_spheres, nc = e->n_capsules, nb = e->n_cuboids;
-    if (ns < 0 || nc < 0 || nb < 0) return fail(ctx, VP_ERR_ARG, "negative primitive count");
-    if ((ns && !e->spheres) || (nc && !e->capsules) || (nb && !e->cuboids))
-        return fail(ctx, VP_ERR_ARG, "primitive table pointer is NULL");
-    const size_t n4 = static_cast<size_t>(ns) + 2 * static_cast<size_t>(nc) + 4 * static_cast<size_t>(nb);
-    if (n4 * 16 > VP_MAX_ENV_BYTES)
-        return fail(ctx, VP_ERR_CAPACITY, "environment packs to %zu bytes > %d", n4 * 16, VP_MAX_ENV_BYTES);
+    size_t n4 = 0;
+    std::string msg;
+    int rc = env_packed_float4(e, &n4, &msg);
+    if (rc) return fail(ctx, rc == 2 ? VP_ERR_CAPACITY : VP_ERR_ARG, "%s", msg.c_str());
     std::vector<float4> h(n4);
-    size_t k = 0;
-    for (int i = 0; i < ns; ++i) {
-        const double *p = e->spheres + 4 * i;
-        if (!finite_all(p, 4) || p[3] < 0) return fail(ctx, VP_ERR_ARG, "sphere %d is malformed", i);
-        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[3])};
-    }
-    for (int i = 0; i < nc; ++i) {
-        const double *p = e->capsules + 7 * i;
-        if (!finite_all(p, 7) || p[6] < 0) return fail(ctx, VP_ERR_ARG, "capsule %d is malformed", i);
-        const double u[3] = {p[3] - p[0], p[4] - p[1], p[5] - p[2]};
-        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[6])};
-        h[k++] = float4{float(u[0]), float(u[1]), float(u[2]), uu > 0 ? float(1.0 / uu) : 0.f};
-    }
-    for (int i = 0; i < nb; ++i) {
-        const double *p = e->cuboids + 15 * i;
-        if (!finite_all(p, 15) || p[12] < 0 || p[13] < 0 || p[14] < 0)
-            return fail(ctx, VP_ERR_ARG, "cuboid %d is malformed", i);
-        const double *c = p, *R = p + 3;
-        for (int a = 0; a < 3; ++a) {
-            // box axis a = column a of R
-            const double ax[3] = {R[0 * 3 + a], R[1 * 3 + a], R[2 * 3 + a]};
-            const double off = ax[0] * c[0] + ax[1] * c[1] + ax[2] * c[2];
-            h[k++] = float4{float(ax[0]), float(ax[1]), float(ax[2]), float(-off)};
-        }
-        h[k++] = float4{float(p[12]), float(p[13]), float(p[14]), 0.f};
-    }
+    EnvView view{};
+    rc = pack_env(e, h.data(), VP_MAX_ENV_BYTES / 16, &view, &msg);
+    if (rc) return fail(ctx, rc == 2 ? VP_ERR_CAPACITY : VP_ERR_ARG, "%s", msg.c_str());
     DeviceGuard g(ctx->device);
     float4 *buf = nullptr;
     if (n4 > 0) {
@@ -385,7 +358,8 @@ extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
         cudaFree(ctx->env_buf);
     }
     ctx->env_buf = buf;
-    ctx->env = EnvView{buf, ns, nc, nb, static_cast<int>(n4)};
+    view.data = buf;
+    ctx->env = view;
     ctx->env_loaded = true;
     batched_invalidate(ctx->batched);
     return VP_OK;
@@ -400,7 +374,7 @@ namespace {
 // opt-in limit; returns false if none does.
 bool plan_block(vp_ctx *ctx, int *block, size_t *smem) {
     for (int b : {128, 64, 32}) {
-        const size_t s = smem_bytes(ctx->env, ctx->robot.n_slots, ctx->robot.n_cslots, b);
+        const size_t s = smem_bytes(ctx->env, ctx->robot.n_links, b);
         if (s <= ctx->smem_optin) {
             *block = b;
             *smem = s;
@@ -443,7 +417,7 @@ extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, 
     if (!plan_block(ctx, &block, &smem))
         return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
     int bps = 0;
-    cudaError_t e = prepare_states(smem, block, &bps);
+    cudaError_t e = prepare_states(lmax_for(ctx->robot.n_links), smem, block, &bps);
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
@@ -501,7 +475,8 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     if (!plan_block(ctx, &block, &smem))
         return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
     int bps = 0;
-    cudaError_t e = prepare_edges_plain(work != nullptr, smem, block, &bps);
+    cudaError_t e = prepare_edges_plain(work != nullptr, lmax_for(ctx->robot.n_links), ctx->robot.simple != 0, smem,
+                                        block, &bps);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges (prepare)");
     if (bps < 1) return fail(ctx, VP_ERR_CAPACITY, "plain edge kernel cannot be resident");
     const int wpb = block / 32;
@@ -509,7 +484,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
         const int D = ctx->robot.n_joints;
         for (int64_t i = 0; i < n_edges && e == cudaSuccess; ++i)
             e = launch_edges_plain(ctx->robot, ctx->env, q0 + i * D, q1 + i * D, counts ? counts + i : nullptr,
-                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_slots, ctx->robot.n_cslots, 32), st);
+                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_links, 32), st);
         return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges (per edge)");
     }
     const int64_t need = (n_edges + wpb - 1) / wpb;

@@ -25,6 +25,7 @@
 
 #include "vp_batched.h"
 #include "vp_device.cuh"
+#include "vp_internal.h"
 
 namespace vp {
 
@@ -133,8 +134,8 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
 
 // Persistent validation of bucketed edges; see the file comment.  STATS adds
 // the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
-template <bool STATS>
-__global__ void __launch_bounds__(kBlock) edges_batched_kernel(
+template <bool STATS, int LMAX, bool SIMPLE>
+__global__ void VP_VALIDATION_BOUNDS edges_batched_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
     const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
     unsigned *status, int *ctrl, unsigned long long *work) {
@@ -148,9 +149,10 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
     float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
     off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
     Stash stash;
-    stash.frames = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_slots) * kFrameFloats * kBlock * sizeof(float);
+    stash.frames = nullptr;
     stash.centres = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>(P.n_links) * kCentreFloats * kBlock * sizeof(float);
+    stash.motion = reinterpret_cast<float *>(smem + off);
     stash.stride = kBlock;
 
     if (threadIdx.x == 0) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
     }
     __syncthreads();
     if (!stage_env(env_sm, env.data, env.n_float4, bar, status)) return;
-    const EnvSm es{env_sm, env_sm + env.ns, env_sm + env.ns + 2 * env.nc, env.ns, env.nc, env.nb};
+    const EnvSm es = env_in_smem(env_sm, env);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int D = P.n_joints;
     float *wbuf = gbuf + wib * 8 * 32;
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
             const WorkRef<STATS> w{&wk, !done && i < k};
             if (i >= k) i = k - 1;
             const float t = static_cast<float>(i) * inv;
-            const bool c = pose_and_check<kStopGroups, STATS>(
+            const bool c = pose_and_check<kStopGroups, STATS, LMAX, SIMPLE>(
                 P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w);
             const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
             if (!done && (gcol || r == R - 1)) {
@@ -261,7 +263,17 @@ __global__ void __launch_bounds__(kBlock) edges_batched_kernel(
 
 size_t batched_smem(const EnvView &env, const RobotParams &P) {
     return static_cast<size_t>(env.n_float4) * 16 + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
-           static_cast<size_t>(P.n_slots * kFrameFloats + P.n_cslots * kCentreFloats) * kBlock * sizeof(float);
+           static_cast<size_t>(P.n_links * kCentreFloats + P.n_joints * 2) * kBlock * sizeof(float);
+}
+
+// The kernel instance for this robot's link count and counting mode.
+using BatchedKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int2 *,
+                               const BatchPlan, uint8_t *, unsigned *, int *, unsigned long long *);
+BatchedKernel batched_kernel_for(const RobotParams &P, bool stats) {
+    const bool small = lmax_for(P.n_links) <= 9, simple = P.simple != 0;
+    if (stats) return small ? edges_batched_kernel<true, 9, false> : edges_batched_kernel<true, 17, false>;
+    if (small) return simple ? edges_batched_kernel<false, 9, true> : edges_batched_kernel<false, 9, false>;
+    return simple ? edges_batched_kernel<false, 17, true> : edges_batched_kernel<false, 17, false>;
 }
 
 // ---------------------------------------------------------------------------
@@ -342,14 +354,12 @@ int prepare_kernel(const BatchedArgs &a, size_t *smem, int *grid, std::string *m
         *msg = "environment and frame stash exceed shared memory";
         return 1;
     }
-    cudaError_t e = cudaFuncSetAttribute(edges_batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(*smem));
+    const BatchedKernel k0 = batched_kernel_for(*a.robot, false), k1 = batched_kernel_for(*a.robot, true);
+    cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(*smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(edges_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(*smem));
+        e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(*smem));
     int bps = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, edges_batched_kernel<false>, kBlock, *smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k0, kBlock, *smem);
     if (e != cudaSuccess) return set_err(msg, "batched kernel attributes", e);
     if (bps < 1) {
         *msg = "batched kernel cannot be resident";
@@ -371,12 +381,8 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_
     // external event-record nodes, so the events time the kernel when replayed from the graph
     if (a.ev_start) e = cudaEventRecordWithFlags(a.ev_start, s, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    if (work)
-        edges_batched_kernel<true><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, plan, valid,
-                                                              a.status, im->ctrl, work);
-    else
-        edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, plan, valid,
-                                                               a.status, im->ctrl, nullptr);
+    batched_kernel_for(*a.robot, work != nullptr)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm,
+                                                                            plan, valid, a.status, im->ctrl, work);
     e = cudaGetLastError();
     if (e == cudaSuccess && a.ev_stop) e = cudaEventRecordWithFlags(a.ev_stop, s, cudaEventRecordExternal);
     return e;
@@ -529,8 +535,9 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
                 e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
                 if (e != cudaSuccess) break;
                 cudaEventRecord(t0, s);
-                edges_batched_kernel<false><<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm, p,
-                                                                       tv, a.status, im->ctrl, nullptr);
+                batched_kernel_for(*a.robot, false)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1,
+                                                                               im->perm, p, tv, a.status, im->ctrl,
+                                                                               nullptr);
                 cudaEventRecord(t1, s);
                 e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaGetLastError();

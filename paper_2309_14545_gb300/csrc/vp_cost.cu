@@ -124,9 +124,10 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
     Stash stash;
     stash.frames = reinterpret_cast<float *>(smem + off);
     stash.centres = nullptr;
+    stash.motion = nullptr;
     stash.stride = static_cast<int>(blockDim.x);
     if (!stage_env(env_sm, env.data, env.n_float4, bar, status)) return;
-    const EnvSm es{env_sm, env_sm + env.ns, env_sm + env.ns + 2 * env.nc, env.ns, env.nc, env.nb};
+    const EnvSm es = env_in_smem(env_sm, env);
     const int D = P.n_joints;
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {

@@ -14,6 +14,17 @@
 
 #include "vp_types.h"
 
+// Launch bounds of the validation kernels: 128 threads per block and, if
+// VP_MIN_BLOCKS > 0, at least that many resident blocks per SM (a register cap).
+#ifndef VP_MIN_BLOCKS
+#define VP_MIN_BLOCKS 0
+#endif
+#if VP_MIN_BLOCKS > 0
+#define VP_VALIDATION_BOUNDS __launch_bounds__(128, VP_MIN_BLOCKS)
+#else
+#define VP_VALIDATION_BOUNDS __launch_bounds__(128)
+#endif
+
 namespace vp {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -40,15 +51,30 @@ __device__ __forceinline__ float3 fr_apply(const Fr &f, float x, float y, float 
                        fmaf(f.r6, x, fmaf(f.r7, y, fmaf(f.r8, z, f.pz))));
 }
 
-// f <- f * origin_j * M_j(q): one joint of the chain.
-__device__ __forceinline__ void apply_joint(const JointC &J, float q, Fr &f) {
+// The joint's motion parameters: (sin q, cos q) for a revolute joint, (q, 0)
+// for a prismatic one.
+__device__ __forceinline__ void joint_motion(const JointC &J, float q, float &s, float &c) {
+    if (J.meta & kMetaPrismatic) {
+        s = q;
+        c = 0.f;
+    } else {
+        sincosf(q, &s, &c);
+    }
+}
+
+// f <- f * origin_j * M_j: one joint of the chain, from its motion
+// parameters (s, c) as given by joint_motion.  SIMPLE: the robot has only
+// canonical axes (x, y, z) and identity origin rotations, so the code for
+// general ones is left out.
+template <bool SIMPLE = false>
+__device__ __forceinline__ void apply_joint_sc(const JointC &J, float s, float c, Fr &f) {
     const int meta = J.meta;
     // translation of the fixed origin, in the parent frame
     const float tx = J.o[3], ty = J.o[7], tz = J.o[11];
     f.px = fmaf(f.r0, tx, fmaf(f.r1, ty, fmaf(f.r2, tz, f.px)));
     f.py = fmaf(f.r3, tx, fmaf(f.r4, ty, fmaf(f.r5, tz, f.py)));
     f.pz = fmaf(f.r6, tx, fmaf(f.r7, ty, fmaf(f.r8, tz, f.pz)));
-    if (!(meta & kMetaOriginRotIdentity)) {
+    if (!SIMPLE && !(meta & kMetaOriginRotIdentity)) {
         const float *o = J.o;
         Fr g = f;
         f.r0 = fmaf(g.r0, o[0], fmaf(g.r1, o[4], g.r2 * o[8]));
@@ -62,14 +88,13 @@ __device__ __forceinline__ void apply_joint(const JointC &J, float q, Fr &f) {
         f.r8 = fmaf(g.r6, o[2], fmaf(g.r7, o[6], g.r8 * o[10]));
     }
     if (meta & kMetaPrismatic) {
+        const float q = s;
         const float ax = J.ax[0] * q, ay = J.ax[1] * q, az = J.ax[2] * q;
         f.px = fmaf(f.r0, ax, fmaf(f.r1, ay, fmaf(f.r2, az, f.px)));
         f.py = fmaf(f.r3, ax, fmaf(f.r4, ay, fmaf(f.r5, az, f.py)));
         f.pz = fmaf(f.r6, ax, fmaf(f.r7, ay, fmaf(f.r8, az, f.pz)));
         return;
     }
-    float s, c;
-    sincosf(q, &s, &c);
     const int axis = (meta >> kMetaAxisShift) & 3;
     if (axis == kAxisZ) {
         // columns 0, 1 rotate: c0' = c c0 + s c1, c1' = c c1 - s c0
@@ -89,7 +114,7 @@ __device__ __forceinline__ void apply_joint(const JointC &J, float q, Fr &f) {
         f.r1 = fmaf(c, a0, s * f.r2); f.r2 = fmaf(c, f.r2, -s * a0);
         f.r4 = fmaf(c, a1, s * f.r5); f.r5 = fmaf(c, f.r5, -s * a1);
         f.r7 = fmaf(c, a2, s * f.r8); f.r8 = fmaf(c, f.r8, -s * a2);
-    } else {
+    } else if (!SIMPLE) {
         // Rodrigues: M = c I + (1 - c) a a^T + s [a]x, then R <- R M
         const float x = J.ax[0], y = J.ax[1], z = J.ax[2], v = 1.f - c;
         const float m00 = fmaf(v * x, x, c), m01 = fmaf(v * x, y, -s * z), m02 = fmaf(v * x, z, s * y);
@@ -106,6 +131,13 @@ __device__ __forceinline__ void apply_joint(const JointC &J, float q, Fr &f) {
         f.r7 = fmaf(g.r6, m01, fmaf(g.r7, m11, g.r8 * m21));
         f.r8 = fmaf(g.r6, m02, fmaf(g.r7, m12, g.r8 * m22));
     }
+}
+
+// f <- f * origin_j * M_j(q).
+__device__ __forceinline__ void apply_joint(const JointC &J, float q, Fr &f) {
+    float s, c;
+    joint_motion(J, q, s, c);
+    apply_joint_sc(J, s, c, f);
 }
 
 // ---------------------------------------------------------------------------
@@ -190,14 +222,17 @@ __device__ __forceinline__ bool stage_env(float4 *dst, const float4 *src, int n_
 
 // ---------------------------------------------------------------------------
 // per-lane stash in shared memory, slot-major and lane-interleaved (conflict
-// free): full frames of branch-point links (a joint whose parent is not the
-// previous joint reads its parent's frame here) and world centres of the
-// bounding spheres of links that are the earlier member of a self pair.
+// free): full frames of branch-point links (used by the FK and cost kernels)
+// and the world centres of the links' bounding spheres (validation).
 
 struct Stash {
     float *frames;   // [n_frame_slots][12][stride]
-    float *centres;  // [n_centre_slots][3][stride]
+    float *centres;  // [n_links][3][stride]
+    float *motion;   // [n_joints][2][stride]: (sin q, cos q) or (q, 0) of each joint
     int stride;      // blockDim.x
+    __device__ __forceinline__ float &mo(int j, int k) const {
+        return motion[(j * 2 + k) * stride + threadIdx.x];
+    }
     __device__ __forceinline__ float &fr(int slot, int k) const {
         return frames[(slot * 12 + k) * stride + threadIdx.x];
     }
@@ -232,10 +267,24 @@ template <class QF>
 __device__ __forceinline__ void recompute_frame(const RobotParams &P, int l, const QF &qf, Fr &g) {
     fr_identity(g);
     unsigned m = P.links[l].path;
+#pragma unroll 1
     while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
         apply_joint(P.joints[j], qf(j), g);
+    }
+}
+
+// The same from the motion parameters the posing pass kept (FMAs only).
+template <bool SIMPLE>
+__device__ __forceinline__ void recompute_frame_cached(const RobotParams &P, int l, const Stash &st, Fr &g) {
+    fr_identity(g);
+    unsigned m = P.links[l].path;
+#pragma unroll 1
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        apply_joint_sc<SIMPLE>(P.joints[j], st.mo(j, 0), st.mo(j, 1), g);
     }
 }
 
@@ -263,7 +312,20 @@ struct EnvSm {
     const float4 *cap;  // [2 nc]
     const float4 *box;  // [4 nb]
     int ns, nc, nb;
+    int kind_order;     // kinds in visiting order, 4 bits each
 };
+
+__device__ __forceinline__ EnvSm env_in_smem(const float4 *sm, const EnvView &env) {
+    EnvSm e;
+    e.sph = sm;
+    e.cap = sm + env.ns;
+    e.box = sm + env.ns + 2 * env.nc;
+    e.ns = env.ns;
+    e.nc = env.nc;
+    e.nb = env.nb;
+    e.kind_order = env.kind_order;
+    return e;
+}
 
 // Early-exit rules.  Every vote spans the full warp; a warp may hold one
 // edge (kStopAny: stop as soon as any lane collides), independent states
@@ -291,72 +353,67 @@ __device__ __forceinline__ bool wants(const Ctl &c, bool v) {
     return MODE == kStopGroups ? (v && !c.idle) : v;
 }
 
-// Coarse tests issued per warp vote, per primitive kind (independent
-// dependency chains for the schedulers to interleave).
-#ifndef VP_UNROLL_SPHERE
-#define VP_UNROLL_SPHERE 8
-#endif
-#ifndef VP_UNROLL_CAPSULE
-#define VP_UNROLL_CAPSULE 8
-#endif
-#ifndef VP_UNROLL_CUBOID
-#define VP_UNROLL_CUBOID 8
-#endif
+// ---------------------------------------------------------------------------
+// the check of one configuration
 
-// Primitive kinds: float4 words per primitive and the ball test.
-struct SphereKind {
-    static constexpr int kWords = 1;
+// Primitive kinds: float4 words per primitive, the ball test, the work counters.
+template <int KIND>
+struct Kind;
+template <>
+struct Kind<0> {
+    static constexpr int kWords = 1, kCoarse = VP_WORK_COARSE_SPHERE, kFine = VP_WORK_FINE_SPHERE;
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) { return hit_sphere(c, r, o[0]); }
 };
-struct CapsuleKind {
-    static constexpr int kWords = 2;
+template <>
+struct Kind<1> {
+    static constexpr int kWords = 2, kCoarse = VP_WORK_COARSE_CAPSULE, kFine = VP_WORK_FINE_CAPSULE;
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
         return hit_capsule(c, r, o[0], o[1]);
     }
 };
-struct CuboidKind {
-    static constexpr int kWords = 4;
+template <>
+struct Kind<2> {
+    static constexpr int kWords = 4, kCoarse = VP_WORK_COARSE_CUBOID, kFine = VP_WORK_FINE_CUBOID;
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
         return hit_cuboid(c, r, o[0], o[1], o[2], o[3]);
     }
 };
 
-// One primitive kind against link l: coarse tests of the link's bounding
-// sphere on U primitives at a time (independent chains, one warp vote per
-// chunk), then fine tests of the link's spheres on each primitive some lane's
-// coarse sphere touched.  Returns the group's stop decision.
-template <class K, int U, int MODE, bool STATS>
-__device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, const Fr &f, float3 cl, float Rl,
-                                         const float4 *prims, int n, const Ctl &ctl, bool &col,
-                                         const WorkRef<STATS> &w, int fine_counter) {
-    for (int o0 = 0; o0 < n; o0 += U) {
+// Every primitive of one kind (largest first) against every link's bounding
+// sphere at once -- independent tests for the scheduler -- then the fine
+// spheres of each link some lane's coarse test hit.  Returns the warp's stop
+// decision.
+template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE>
+__device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, int n, const float *cx,
+                                          const float *cy, const float *cz, const Stash &stash, const Ctl &ctl,
+                                          bool &col, const WorkRef<STATS> &w) {
+    using K = Kind<KIND>;
+    const unsigned lmask = P.link_mask;
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        float4 o[K::kWords];
+#pragma unroll
+        for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
         unsigned bits = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (o0 + u < n) {
-                float4 ob[K::kWords];
-#pragma unroll
-                for (int k = 0; k < K::kWords; ++k) ob[k] = prims[(o0 + u) * K::kWords + k];
-                bits |= static_cast<unsigned>(K::hit(cl, Rl, ob)) << u;
-            }
-        }
+        for (int l = 0; l < LMAX; ++l)
+            if ((lmask >> l) & 1u)
+                bits |= static_cast<unsigned>(K::hit(make_float3(cx[l], cy[l], cz[l]), P.links[l].bs.w, o)) << l;
+        w.add(K::kCoarse, __popc(lmask));
         if (MODE == kStopGroups && ctl.idle) bits = 0;
-        unsigned any = 0;
-        if (__any_sync(kFull, bits != 0)) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) any |= static_cast<unsigned>(__any_sync(kFull, (bits >> u) & 1u)) << u;
-        }
+        unsigned any = __reduce_or_sync(kFull, bits);
         while (any) {
-            const int u = __ffs(any) - 1;
+            const int l = __ffs(any) - 1;
             any &= any - 1;
-            const bool h = (bits >> u) & 1u;
-            float4 ob[K::kWords];
-#pragma unroll
-            for (int k = 0; k < K::kWords; ++k) ob[k] = prims[(o0 + u) * K::kWords + k];
-            w.add(fine_counter, L.s1 - L.s0);
+            const LinkC &L = P.links[l];
+            Fr f;
+            recompute_frame_cached<SIMPLE>(P, l, stash, f);
+            w.add(K::kFine, L.s1 - L.s0);
+            const bool h = (bits >> l) & 1u;
+#pragma unroll 1
             for (int s = L.s0; s < L.s1; ++s) {
                 const float4 sp = P.spheres[s];
-                col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, ob);
+                col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, o);
             }
             if (group_stop<MODE>(ctl, col)) return true;
         }
@@ -364,99 +421,101 @@ __device__ __forceinline__ bool env_pass(const RobotParams &P, const LinkC &L, c
     return false;
 }
 
-// Check link l (posed as f) against the environment, coarse then fine, then
-// its self-collision groups.  `col` accumulates this lane's collision; the
-// return value is the group's stop decision.
-template <int MODE, bool STATS, class QF>
-__device__ __forceinline__ bool check_link(const RobotParams &P, int l, const Fr &f, float3 &cl, const QF &qf,
-                                           const EnvSm &env, const Stash &stash, const Ctl &ctl, bool &col,
-                                           const WorkRef<STATS> &w) {
-    const LinkC &L = P.links[l];
-    const bool has_spheres = L.s0 < L.s1;
-    if (has_spheres) {
-        cl = fr_apply(f, L.bs.x, L.bs.y, L.bs.z);
-        const float Rl = L.bs.w;
-        w.add(VP_WORK_LINK_CENTRES, 1);
-        w.add(VP_WORK_COARSE_SPHERE, env.ns);
-        w.add(VP_WORK_COARSE_CAPSULE, env.nc);
-        w.add(VP_WORK_COARSE_CUBOID, env.nb);
-        if (env_pass<SphereKind, VP_UNROLL_SPHERE, MODE, STATS>(P, L, f, cl, Rl, env.sph, env.ns, ctl, col, w, VP_WORK_FINE_SPHERE))
-            return true;
-        if (env_pass<CapsuleKind, VP_UNROLL_CAPSULE, MODE, STATS>(P, L, f, cl, Rl, env.cap, env.nc, ctl, col, w,
-                                                  VP_WORK_FINE_CAPSULE))
-            return true;
-        if (env_pass<CuboidKind, VP_UNROLL_CUBOID, MODE, STATS>(P, L, f, cl, Rl, env.box, env.nb, ctl, col, w,
-                                                 VP_WORK_FINE_CUBOID))
-            return true;
+// Pose one configuration and check it (Sec. III-B/C/D):
+//   1. pose every link (FK is cheap next to the checks), keeping each
+//      joint's (sin, cos) and the world centre of each link's bounding
+//      sphere in the per-lane stash;
+//   2. self pairs: link-pair bounding-sphere test, then the sphere pairs of
+//      the link pairs some lane's coarse test hit;
+//   3. primitives, kind by kind, each against every link's bounding sphere,
+//      then fine spheres where a coarse test hit.
+// Frames needed by fine tests are recomputed from the kept (sin, cos).  The
+// order of checks is chosen for early exit: a colliding configuration is
+// most often found by a self pair or a large primitive; it does not change
+// the verdict.  LMAX bounds the link count (centres held in registers).
+// Returns this lane's collision flag; the warp stops early per MODE.
+template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+__device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
+                                               const Stash &stash, const Ctl &ctl, const WorkRef<STATS> &w) {
+    bool col = false;
+    const int D = P.n_joints;
+    w.add(VP_WORK_STATES, 1);
+    // 1. pose
+    {
+        Fr f;
+        fr_identity(f);
+        for (int l = 0; l <= D; ++l) {
+            if (l > 0) {
+                const JointC &J = P.joints[l - 1];
+                const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+                if (pm == kParentBase)
+                    fr_identity(f);
+                else if (pm != kParentPrev)
+                    recompute_frame_cached<SIMPLE>(P, (J.meta >> kMetaParentLinkShift) & 0xFF, stash, f);
+                float ms, mc;
+                joint_motion(J, qf(l - 1), ms, mc);
+                stash.mo(l - 1, 0) = ms;
+                stash.mo(l - 1, 1) = mc;
+                apply_joint_sc<SIMPLE>(J, ms, mc, f);
+            }
+            const LinkC &L = P.links[l];
+            if (L.s0 < L.s1) {
+                stash.store_centre(l, fr_apply(f, L.bs.x, L.bs.y, L.bs.z));
+                w.add(VP_WORK_LINK_CENTRES, 1);
+            }
+        }
     }
-    // self pairs whose later link is l
-    for (int g = L.g0; g < L.g1; ++g) {
+    // 2. self pairs
+    for (int g = 0; g < P.n_groups; ++g) {
         const GroupC G = P.groups[g];
-        const LinkC &La = P.links[G.la];
-        float3 ca;
-        if (G.slot_a >= 0)
-            ca = stash.centre(G.slot_a);
-        else if (G.slot_a == kSlotBase)
-            ca = make_float3(La.bs.x, La.bs.y, La.bs.z);
-        else
-            ca = cl;
-        const float dx = ca.x - cl.x, dy = ca.y - cl.y, dz = ca.z - cl.z;
-        const float rr = La.bs.w + L.bs.w;
+        const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
+        const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+        const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
         const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
         w.add(VP_WORK_PAIR_COARSE, 1);
         if (__any_sync(kFull, wants<MODE>(ctl, h))) {
-            Fr fa;
-            if (G.slot_a >= 0)
-                recompute_frame(P, G.la, qf, fa);
-            else if (G.slot_a == kSlotBase)
-                fr_identity(fa);
+            Fr fa, fb;
+            recompute_frame_cached<SIMPLE>(P, G.lb, stash, fb);
+            if (G.la == G.lb)
+                fa = fb;
             else
-                fa = f;
+                recompute_frame_cached<SIMPLE>(P, G.la, stash, fa);
             w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+#pragma unroll 1
             for (int p = G.p0; p < G.p1; ++p) {
                 const PairC pr = P.pairs[p];
                 const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
                 const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
-                const float3 b = fr_apply(f, sb.x, sb.y, sb.z);
+                const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
                 const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
                 const float r2 = sa.w + sb.w;
                 col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
             }
-            if (group_stop<MODE>(ctl, col)) return true;
+            if (group_stop<MODE>(ctl, col)) return col;
         }
     }
-    return false;
-}
-
-// Pose a configuration link by link and check each link as soon as it is
-// posed (Sec. III-D: checks interleaved into FK; links after a collision are
-// never posed).  qf(j) returns joint j's coordinate for this lane.
-// Returns this lane's collision flag (the warp stops early per MODE).
-template <int MODE, bool STATS, class QF>
-__device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
-                                               const Stash &stash, const Ctl &ctl, const WorkRef<STATS> &w) {
-    bool col = false;
-    Fr f;
-    fr_identity(f);
-    float3 cl = make_float3(0.f, 0.f, 0.f);
-    w.add(VP_WORK_STATES, 1);
-    const int D = P.n_joints;
-    // link 0 is the base (identity frame); link l > 0 follows joint l - 1.
-    // One call site for check_link keeps the kernel's code compact.
-    for (int l = 0; l <= D; ++l) {
-        if (l > 0) {
-            const JointC &J = P.joints[l - 1];
-            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
-            if (pm == kParentBase)
-                fr_identity(f);
-            else if (pm != kParentPrev)
-                stash.load_frame(pm, f);
-            apply_joint(J, qf(l - 1), f);
+    // 3. primitives against every link
+    float cx[LMAX], cy[LMAX], cz[LMAX];
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+        cx[l] = cy[l] = cz[l] = 0.f;
+        if ((P.link_mask >> l) & 1u) {
+            const float3 c = stash.centre(l);
+            cx[l] = c.x;
+            cy[l] = c.y;
+            cz[l] = c.z;
         }
-        if (check_link<MODE, STATS>(P, l, f, cl, qf, env, stash, ctl, col, w)) return col;
-        const LinkC &Lk = P.links[l];
-        if (Lk.slot >= 0) stash.store_frame(Lk.slot, f);
-        if (Lk.cslot >= 0) stash.store_centre(Lk.cslot, cl);
+    }
+    for (int ki = 0; ki < 3; ++ki) {
+        const int kind = (env.kind_order >> (4 * ki)) & 15;
+        bool stop;
+        if (kind == 0)
+            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.ns, cx, cy, cz, stash, ctl, col, w);
+        else if (kind == 1)
+            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.nc, cx, cy, cz, stash, ctl, col, w);
+        else
+            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.nb, cx, cy, cz, stash, ctl, col, w);
+        if (stop) return col;
     }
     return col;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "vp_types.h"
 
@@ -18,17 +19,26 @@ struct SmemPlan {
     int blocks_per_sm;  // resident blocks per SM at this size
 };
 
-size_t smem_bytes(const EnvView &env, int n_frame_slots, int n_centre_slots, int block);
+// Validation kernels: environment, mbarrier, per-warp buffers, link centres.
+size_t smem_bytes(const EnvView &env, int n_links, int block);
+
+// Environment packing (host): float4 count, and the packed buffer with its
+// view (data pointer left null).  0 = ok, 1 = bad argument, 2 = capacity.
+int env_packed_float4(const vp_env_desc *e, size_t *n4, std::string *msg);
+int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view, std::string *msg);
+
+// Link-count bound of the validation kernels' register-held link centres.
+inline int lmax_for(int n_links) { return n_links <= 9 ? 9 : 17; }
 
 // Plain edge validation: one warp per edge, static grid-stride over edges.
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t prepare_edges_plain(bool stats, size_t smem, int block, int *blocks_per_sm);
+cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, size_t smem, int block, int *blocks_per_sm);
 
 cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
                           unsigned *status, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t prepare_states(size_t smem, int block, int *blocks_per_sm);
+cudaError_t prepare_states(int lmax, size_t smem, int block, int *blocks_per_sm);
 
 cudaError_t launch_fk(const RobotParams &P, const float *q, int64_t N, float *centres, int grid, int block,
                       size_t smem, cudaStream_t st);

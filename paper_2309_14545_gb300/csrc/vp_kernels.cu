@@ -7,11 +7,10 @@
 
 namespace vp {
 
-size_t smem_bytes(const EnvView &env, int n_frame_slots, int n_centre_slots, int block) {
+size_t smem_bytes(const EnvView &env, int n_links, int block) {
     const size_t warps = static_cast<size_t>((block + 31) / 32);
     return static_cast<size_t>(env.n_float4) * 16 + 16 + warps * 32 * sizeof(float) +
-           static_cast<size_t>(n_frame_slots * kFrameFloats + n_centre_slots * kCentreFloats) * block *
-               sizeof(float);
+           static_cast<size_t>(n_links * kCentreFloats + (n_links - 1) * 2) * block * sizeof(float);
 }
 
 // State count of an edge from its largest joint displacement (float32, IEEE
@@ -37,22 +36,12 @@ __device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &e
     off += 16;
     c.warp_buf = reinterpret_cast<float *>(smem + off);
     off += static_cast<size_t>((blockDim.x + 31) / 32) * 32 * sizeof(float);
-    c.stash.frames = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_slots) * kFrameFloats * blockDim.x * sizeof(float);
+    c.stash.frames = nullptr;
     c.stash.centres = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>(P.n_links) * kCentreFloats * blockDim.x * sizeof(float);
+    c.stash.motion = reinterpret_cast<float *>(smem + off);
     c.stash.stride = static_cast<int>(blockDim.x);
     return c;
-}
-
-__device__ __forceinline__ EnvSm env_view(const float4 *sm, const EnvView &env) {
-    EnvSm e;
-    e.sph = sm;
-    e.cap = sm + env.ns;
-    e.box = sm + env.ns + 2 * env.nc;
-    e.ns = env.ns;
-    e.nc = env.nc;
-    e.nb = env.nb;
-    return e;
 }
 
 template <bool STATS>
@@ -70,8 +59,8 @@ __device__ __forceinline__ void flush_work(Work &wk, unsigned long long *work, i
 // One warp per edge.  Lane j of the warp checks states j*R + r in round r
 // (R = ceil(k/32) rounds): the rake of Sec. III-D, 32 spread states per
 // round.  Lanes past the end park on the last state.
-template <bool STATS>
-__global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+template <bool STATS, int LMAX, bool SIMPLE>
+__global__ void VP_VALIDATION_BOUNDS edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                           const float *__restrict__ q0, const float *__restrict__ q1,
                                                           const int32_t *__restrict__ counts, const float res,
                                                           const long long E, uint8_t *__restrict__ valid,
@@ -79,7 +68,7 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemCarve sc = carve(smem, env, P);
     if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
-    const EnvSm es = env_view(sc.env, env);
+    const EnvSm es = env_in_smem(sc.env, env);
     const Stash &stash = sc.stash;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     float *wq0 = sc.warp_buf + wib * 32;
@@ -131,7 +120,7 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
                 if (!real) i = k - 1;
                 const float t = static_cast<float>(i) * inv;
                 const WorkRef<STATS> w{&wk, real};
-                const bool c = pose_and_check<kStopAny, STATS>(
+                const bool c = pose_and_check<kStopAny, STATS, LMAX, SIMPLE>(
                     P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, Ctl{kFull, false}, w);
                 if (__any_sync(kFull, c)) {
                     collided = true;
@@ -150,13 +139,14 @@ __global__ void __launch_bounds__(128) edges_plain_kernel(const __grid_constant_
 
 // One lane per configuration; lanes are independent (a warp stops once all
 // its lanes collided).
-__global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+template <int LMAX>
+__global__ void VP_VALIDATION_BOUNDS states_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                      const float *__restrict__ q, const long long N,
                                                      uint8_t *__restrict__ valid, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemCarve sc = carve(smem, env, P);
     if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
-    const EnvSm es = env_view(sc.env, env);
+    const EnvSm es = env_in_smem(sc.env, env);
     const Stash &stash = sc.stash;
     const int lane = threadIdx.x & 31;
     const int D = P.n_joints;
@@ -170,7 +160,7 @@ __global__ void __launch_bounds__(128) states_kernel(const __grid_constant__ Rob
         bool fin = true;
         for (int j = 0; j < D; ++j) fin &= isfinite(qi[j]);
         const WorkRef<false> w{nullptr, false};
-        const bool c = pose_and_check<kStopAll, false>(P, [qi](int j) { return qi[j]; }, es, stash, Ctl{kFull, false}, w);
+        const bool c = pose_and_check<kStopAll, false, LMAX, false>(P, [qi](int j) { return qi[j]; }, es, stash, Ctl{kFull, false}, w);
         if (real) valid[i] = (c || !fin) ? 0 : 1;
     }
 }
@@ -182,6 +172,7 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ RobotPa
     Stash stash;
     stash.frames = reinterpret_cast<float *>(smem);
     stash.centres = nullptr;
+    stash.motion = nullptr;
     stash.stride = static_cast<int>(blockDim.x);
     const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -237,28 +228,38 @@ static cudaError_t prepare(K kernel, size_t smem, int block, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
 }
 
-cudaError_t prepare_edges_plain(bool stats, size_t smem, int block, int *blocks_per_sm) {
-    return stats ? prepare(edges_plain_kernel<true>, smem, block, blocks_per_sm)
-                 : prepare(edges_plain_kernel<false>, smem, block, blocks_per_sm);
+// Instances: the counting variant always takes the general joint code.
+using PlainKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int32_t *,
+                             const float, const long long, uint8_t *, unsigned *, unsigned long long *);
+static PlainKernel plain_kernel_for(int lmax, bool stats, bool simple) {
+    if (stats) return lmax <= 9 ? edges_plain_kernel<true, 9, false> : edges_plain_kernel<true, 17, false>;
+    if (lmax <= 9) return simple ? edges_plain_kernel<false, 9, true> : edges_plain_kernel<false, 9, false>;
+    return simple ? edges_plain_kernel<false, 17, true> : edges_plain_kernel<false, 17, false>;
+}
+
+cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, size_t smem, int block, int *blocks_per_sm) {
+    return prepare(plain_kernel_for(lmax, stats, simple), smem, block, blocks_per_sm);
 }
 
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st) {
-    if (work)
-        edges_plain_kernel<true><<<grid, block, smem, st>>>(P, env, q0, q1, counts, res, E, valid, status, work);
-    else
-        edges_plain_kernel<false><<<grid, block, smem, st>>>(P, env, q0, q1, counts, res, E, valid, status, work);
+    plain_kernel_for(lmax_for(P.n_links), work != nullptr, P.simple != 0)<<<grid, block, smem, st>>>(
+        P, env, q0, q1, counts, res, E, valid, status, work);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_states(size_t smem, int block, int *blocks_per_sm) {
-    return prepare(states_kernel, smem, block, blocks_per_sm);
+cudaError_t prepare_states(int lmax, size_t smem, int block, int *blocks_per_sm) {
+    return lmax <= 9 ? prepare(states_kernel<9>, smem, block, blocks_per_sm)
+                     : prepare(states_kernel<17>, smem, block, blocks_per_sm);
 }
 
 cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
                           unsigned *status, int grid, int block, size_t smem, cudaStream_t st) {
-    states_kernel<<<grid, block, smem, st>>>(P, env, q, N, valid, status);
+    if (lmax_for(P.n_links) <= 9)
+        states_kernel<9><<<grid, block, smem, st>>>(P, env, q, N, valid, status);
+    else
+        states_kernel<17><<<grid, block, smem, st>>>(P, env, q, N, valid, status);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ struct DeviceSetup {
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[kMaxDevices];
 
-// Per-thread host staging for the packed environment (no heap use).
+// Per-thread host staging for the packed environment.
 thread_local float4 t_env_host[VP_NOALLOC_MAX_ENV_BYTES / 16];
 
 void set_msg(char *buf, int32_t len, const char *fmt, ...) {
@@ -87,71 +87,6 @@ vp_status device_scratch(int dev, DeviceSetup **out, char *msg, int32_t msg_len)
     return VP_OK;
 }
 
-bool finite_n(const double *p, int n) {
-    for (int i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
-}
-
-// Pack the environment into t_env_host in the kernel's float4 layout;
-// returns the float4 count or -1 (message set).
-int pack_env(const vp_env_desc *e, char *msg, int32_t msg_len, vp_status *st) {
-    const int ns = e->n_spheres, nc = e->n_capsules, nb = e->n_cuboids;
-    *st = VP_ERR_ARG;
-    if (ns < 0 || nc < 0 || nb < 0) {
-        set_msg(msg, msg_len, "negative primitive count");
-        return -1;
-    }
-    if ((ns && !e->spheres) || (nc && !e->capsules) || (nb && !e->cuboids)) {
-        set_msg(msg, msg_len, "primitive table pointer is NULL");
-        return -1;
-    }
-    const double n4 = static_cast<double>(ns) + 2.0 * nc + 4.0 * nb;
-    if (n4 * 16 > VP_NOALLOC_MAX_ENV_BYTES) {
-        set_msg(msg, msg_len, "environment packs to %.0f bytes, more than the %d-byte static scratch", n4 * 16,
-                VP_NOALLOC_MAX_ENV_BYTES);
-        *st = VP_ERR_CAPACITY;
-        return -1;
-    }
-    float4 *h = t_env_host;
-    int k = 0;
-    for (int i = 0; i < ns; ++i) {
-        const double *p = e->spheres + 4 * i;
-        if (!finite_n(p, 4) || p[3] < 0) {
-            set_msg(msg, msg_len, "malformed sphere");
-            return -1;
-        }
-        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[3])};
-    }
-    for (int i = 0; i < nc; ++i) {
-        const double *p = e->capsules + 7 * i;
-        if (!finite_n(p, 7) || p[6] < 0) {
-            set_msg(msg, msg_len, "malformed capsule");
-            return -1;
-        }
-        const double u[3] = {p[3] - p[0], p[4] - p[1], p[5] - p[2]};
-        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        h[k++] = float4{float(p[0]), float(p[1]), float(p[2]), float(p[6])};
-        h[k++] = float4{float(u[0]), float(u[1]), float(u[2]), uu > 0 ? float(1.0 / uu) : 0.f};
-    }
-    for (int i = 0; i < nb; ++i) {
-        const double *p = e->cuboids + 15 * i;
-        if (!finite_n(p, 15) || p[12] < 0 || p[13] < 0 || p[14] < 0) {
-            set_msg(msg, msg_len, "malformed cuboid");
-            return -1;
-        }
-        const double *c = p, *R = p + 3;
-        for (int a = 0; a < 3; ++a) {
-            const double ax[3] = {R[0 * 3 + a], R[1 * 3 + a], R[2 * 3 + a]};
-            const double off = ax[0] * c[0] + ax[1] * c[1] + ax[2] * c[2];
-            h[k++] = float4{float(ax[0]), float(ax[1]), float(ax[2]), float(-off)};
-        }
-        h[k++] = float4{float(p[12]), float(p[13]), float(p[14]), 0.f};
-    }
-    *st = VP_OK;
-    return k;
-}
-
 }  // namespace
 
 extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const vp_env_desc *env,
@@ -182,8 +117,15 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
         set_msg(errbuf, errbuf_len, "robot: %s", perr.c_str());
         return st;
     }
-    const int n4 = pack_env(env, errbuf, errbuf_len, &st);
-    if (n4 < 0) return st;
+    EnvView ev{};
+    std::string emsg;
+    const int prc = pack_env(env, t_env_host, VP_NOALLOC_MAX_ENV_BYTES / 16, &ev, &emsg);
+    if (prc) {
+        if (prc == 2) emsg += " (the static scratch holds " + std::to_string(VP_NOALLOC_MAX_ENV_BYTES) + " bytes)";
+        set_msg(errbuf, errbuf_len, "%s", emsg.c_str());
+        return prc == 2 ? VP_ERR_CAPACITY : VP_ERR_ARG;
+    }
+    const int n4 = ev.n_float4;
     if (n_edges == 0) return VP_OK;
 
     int dev = 0;
@@ -198,11 +140,11 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
 
     unsigned *status = reinterpret_cast<unsigned *>(ds->scratch);
     float4 *env_dev = reinterpret_cast<float4 *>(ds->scratch + kStatusBytes);
-    const EnvView ev{env_dev, env->n_spheres, env->n_capsules, env->n_cuboids, n4};
+    ev.data = env_dev;
     int block = 0;
     size_t smem = 0;
     for (int b : {128, 64, 32}) {
-        const size_t s = smem_bytes(ev, rp.n_slots, rp.n_cslots, b);
+        const size_t s = smem_bytes(ev, rp.n_links, b);
         if (s <= ds->smem_optin) {
             block = b;
             smem = s;
@@ -215,7 +157,7 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int bps = 0;
-    e = prepare_edges_plain(false, smem, block, &bps);
+    e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, smem, block, &bps);
     // the array keeps the previous call's contents: restage the environment
     // and clear the status word on every call
     if (e == cudaSuccess && n4 > 0)

@@ -31,13 +31,9 @@ constexpr int kParentBase = 0xFE;    // the base (identity)
 // any other value: the frame-stash slot holding the parent link's frame
 constexpr int kMetaParentLinkShift = 16;  // 8 bits: the parent link's index
 
-// GroupC::slot_a: the centre-stash slot of the earlier link, or
-constexpr int kSlotSameLink = -1;  // both spheres on the current link
-constexpr int kSlotBase = -2;      // earlier link is the base (identity frame)
-
 // Shared-memory floats per lane for each kind of stash slot.
 constexpr int kFrameFloats = 12;   // frame [R row-major | p] of a branch-point link
-constexpr int kCentreFloats = 3;   // world centre of a self-pair partner's bounding sphere
+constexpr int kCentreFloats = 3;   // world centre of a link's bounding sphere
 
 // Conservative inflation of every link bounding sphere (m): covers float32
 // rounding in the coarse test so a coarse miss never hides a fine hit.
@@ -53,15 +49,14 @@ struct LinkC {  // 32 bytes
     float4 bs;       // bounding sphere: centre (link frame), radius (+eps); radius < 0: no spheres
     int16_t s0, s1;  // fine spheres [s0, s1) in sorted order
     int16_t g0, g1;  // self groups [g0, g1) checked once this link is posed
-    int16_t slot;    // frame-stash slot (branch point), -1 if none
-    int16_t cslot;   // centre-stash slot (earlier self-pair partner), -1 if none
+    int16_t slot;    // frame-stash slot (branch point; FK and cost kernels), -1 if none
     uint16_t path;   // joints from the base to this link (bit j = joint j)
-    int16_t pad;
+    int16_t pad[2];
 };
 
-struct GroupC {      // one link pair (la < lb) and its sphere pairs
+struct GroupC {      // one link pair (la <= lb) and its sphere pairs
     int16_t la;      // earlier link
-    int16_t slot_a;  // centre-stash slot of la, or kSlotSameLink / kSlotBase
+    int16_t lb;      // later link
     int16_t p0, p1;  // pairs [p0, p1)
 };
 
@@ -71,9 +66,9 @@ struct PairC {
 
 struct RobotParams {
     int n_joints, n_links, n_spheres, n_pairs, n_groups;
-    int n_slots;    // frame-stash slots
-    int n_cslots;   // centre-stash slots
-    int pad0;
+    int n_slots;    // frame-stash slots (branch points)
+    unsigned link_mask;  // bit l: link l has spheres
+    int simple;          // 1: canonical axes and identity origin rotations only
     JointC joints[kMaxJoints];
     LinkC links[kMaxLinks];
     float4 spheres[kMaxSpheres];  // local centre, radius (sorted by link)
@@ -84,11 +79,14 @@ struct RobotParams {
 
 // Environment layout (float4 units): spheres [ns] (c, r); capsules [2 nc]
 // ((p0, r), (u = p1 - p0, 1/|u|^2)); cuboids [4 nb] ((a_i, -a_i . c) for the
-// three box axes a_i, then (h, 0)).
+// three box axes a_i, then (h, 0)).  Each kind is stored largest bounding
+// radius first; kind_order lists the kinds (0 sphere, 1 capsule, 2 cuboid;
+// 4 bits each) in order of their largest member.
 struct EnvView {
     const float4 *data;
     int ns, nc, nb;
-    int n_float4;  // total float4 count
+    int n_float4;    // total float4 count
+    int kind_order;  // visiting order of the kinds
 };
 
 }  // namespace vp
