@@ -135,7 +135,7 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
 // Persistent validation of bucketed edges; see the file comment.  STATS adds
 // the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
 template <bool STATS, int LMAX, bool SIMPLE>
-__global__ void VP_VALIDATION_BOUNDS edges_batched_kernel(
+__global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
     const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
     unsigned *status, int *ctrl, unsigned long long *work) {

@@ -14,16 +14,11 @@
 
 #include "vp_types.h"
 
-// Launch bounds of the validation kernels: 128 threads per block and, if
-// VP_MIN_BLOCKS > 0, at least that many resident blocks per SM (a register cap).
-#ifndef VP_MIN_BLOCKS
-#define VP_MIN_BLOCKS 0
-#endif
-#if VP_MIN_BLOCKS > 0
-#define VP_VALIDATION_BOUNDS __launch_bounds__(128, VP_MIN_BLOCKS)
-#else
-#define VP_VALIDATION_BOUNDS __launch_bounds__(128)
-#endif
+// Launch bounds of the validation kernels: 128 threads per block; with up
+// to 9 links the register budget is capped so that `blocks` blocks stay
+// resident per SM (measured best: 6 batched, 5 plain); the 17-link
+// instances keep 4 (128 registers: a tighter cap makes them spill).
+#define VP_VALIDATION_BOUNDS(LMAX, blocks) __launch_bounds__(128, (LMAX) <= 9 ? (blocks) : 4)
 
 namespace vp {
 
@@ -465,33 +460,40 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             }
         }
     }
-    // 2. self pairs
-    for (int g = 0; g < P.n_groups; ++g) {
-        const GroupC G = P.groups[g];
-        const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
-        const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
-        const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
-        const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
-        w.add(VP_WORK_PAIR_COARSE, 1);
-        if (__any_sync(kFull, wants<MODE>(ctl, h))) {
-            Fr fa, fb;
-            recompute_frame_cached<SIMPLE>(P, G.lb, stash, fb);
-            if (G.la == G.lb)
-                fa = fb;
-            else
-                recompute_frame_cached<SIMPLE>(P, G.la, stash, fa);
-            w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+    // 2. self pairs (groups sorted by later link: its frame is reused
+    //    across consecutive groups; the earlier link's too while it repeats)
+    {
+        Fr fa, fb;
+        int la_cached = -1, lb_cached = -1;
+        for (int g = 0; g < P.n_groups; ++g) {
+            const GroupC G = P.groups[g];
+            const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
+            const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+            const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
+            const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+            w.add(VP_WORK_PAIR_COARSE, 1);
+            if (__any_sync(kFull, wants<MODE>(ctl, h))) {
+                if (G.lb != lb_cached) {
+                    recompute_frame_cached<SIMPLE>(P, G.lb, stash, fb);
+                    lb_cached = G.lb;
+                }
+                if (G.la != la_cached) {
+                    recompute_frame_cached<SIMPLE>(P, G.la, stash, fa);
+                    la_cached = G.la;
+                }
+                w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
 #pragma unroll 1
-            for (int p = G.p0; p < G.p1; ++p) {
-                const PairC pr = P.pairs[p];
-                const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
-                const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
-                const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
-                const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
-                const float r2 = sa.w + sb.w;
-                col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+                for (int p = G.p0; p < G.p1; ++p) {
+                    const PairC pr = P.pairs[p];
+                    const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
+                    const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
+                    const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
+                    const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+                    const float r2 = sa.w + sb.w;
+                    col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+                }
+                if (group_stop<MODE>(ctl, col)) return col;
             }
-            if (group_stop<MODE>(ctl, col)) return col;
         }
     }
     // 3. primitives against every link

@@ -60,7 +60,7 @@ __device__ __forceinline__ void flush_work(Work &wk, unsigned long long *work, i
 // (R = ceil(k/32) rounds): the rake of Sec. III-D, 32 spread states per
 // round.  Lanes past the end park on the last state.
 template <bool STATS, int LMAX, bool SIMPLE>
-__global__ void VP_VALIDATION_BOUNDS edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+__global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                           const float *__restrict__ q0, const float *__restrict__ q1,
                                                           const int32_t *__restrict__ counts, const float res,
                                                           const long long E, uint8_t *__restrict__ valid,
@@ -140,7 +140,7 @@ __global__ void VP_VALIDATION_BOUNDS edges_plain_kernel(const __grid_constant__ 
 // One lane per configuration; lanes are independent (a warp stops once all
 // its lanes collided).
 template <int LMAX>
-__global__ void VP_VALIDATION_BOUNDS states_kernel(const __grid_constant__ RobotParams P, const EnvView env,
+__global__ void VP_VALIDATION_BOUNDS(LMAX, 5) states_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                      const float *__restrict__ q, const long long N,
                                                      uint8_t *__restrict__ valid, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
