@@ -269,11 +269,20 @@ size_t batched_smem(const EnvView &env, const RobotParams &P) {
 // The kernel instance for this robot's link count and counting mode.
 using BatchedKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int2 *,
                                const BatchPlan, uint8_t *, unsigned *, int *, unsigned long long *);
+template <int LMAX>
+BatchedKernel batched_instance(bool stats, bool simple) {
+    if (stats) return edges_batched_kernel<true, LMAX, false>;
+    return simple ? edges_batched_kernel<false, LMAX, true> : edges_batched_kernel<false, LMAX, false>;
+}
+
 BatchedKernel batched_kernel_for(const RobotParams &P, bool stats) {
-    const bool small = lmax_for(P.n_links) <= 9, simple = P.simple != 0;
-    if (stats) return small ? edges_batched_kernel<true, 9, false> : edges_batched_kernel<true, 17, false>;
-    if (small) return simple ? edges_batched_kernel<false, 9, true> : edges_batched_kernel<false, 9, false>;
-    return simple ? edges_batched_kernel<false, 17, true> : edges_batched_kernel<false, 17, false>;
+    const bool simple = P.simple != 0;
+    switch (lmax_for(P.n_links)) {
+        case 8: return batched_instance<8>(stats, simple);
+        case 9: return batched_instance<9>(stats, simple);
+        case 15: return batched_instance<15>(stats, simple);
+        default: return batched_instance<17>(stats, simple);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,7 @@
 // resident per SM (measured best: 6 batched, 5 plain); the 17-link
 // instances keep 4 (128 registers: a tighter cap makes them spill).
 #define VP_VALIDATION_BOUNDS(LMAX, blocks) __launch_bounds__(128, (LMAX) <= 9 ? (blocks) : 4)
+// (the 8- and 9-link instances share the first budget, 15 and 17 the second)
 
 namespace vp {
 
@@ -390,10 +391,13 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 #pragma unroll
         for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
         unsigned bits = 0;
+        // no per-link branch: a link without spheres (or past the robot's
+        // last link) sits at 1e30, where every test fails (its squared
+        // distance overflows to +inf; for a cuboid some |a_i . c| >= 1e30
+        // since the box axes span space)
 #pragma unroll
         for (int l = 0; l < LMAX; ++l)
-            if ((lmask >> l) & 1u)
-                bits |= static_cast<unsigned>(K::hit(make_float3(cx[l], cy[l], cz[l]), P.links[l].bs.w, o)) << l;
+            bits |= static_cast<unsigned>(K::hit(make_float3(cx[l], cy[l], cz[l]), P.links[l].bs.w, o)) << l;
         w.add(K::kCoarse, __popc(lmask));
         if (MODE == kStopGroups && ctl.idle) bits = 0;
         unsigned any = __reduce_or_sync(kFull, bits);
@@ -500,7 +504,7 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
     float cx[LMAX], cy[LMAX], cz[LMAX];
 #pragma unroll
     for (int l = 0; l < LMAX; ++l) {
-        cx[l] = cy[l] = cz[l] = 0.f;
+        cx[l] = cy[l] = cz[l] = 1e30f;  // far away: no primitive is within reach
         if ((P.link_mask >> l) & 1u) {
             const float3 c = stash.centre(l);
             cx[l] = c.x;

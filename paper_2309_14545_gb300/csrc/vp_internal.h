@@ -27,8 +27,9 @@ size_t smem_bytes(const EnvView &env, int n_links, int block);
 int env_packed_float4(const vp_env_desc *e, size_t *n4, std::string *msg);
 int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view, std::string *msg);
 
-// Link-count bound of the validation kernels' register-held link centres.
-inline int lmax_for(int n_links) { return n_links <= 9 ? 9 : 17; }
+// Link-count bound of the validation kernels' register-held link centres
+// (instances exist for 8, 9, 15 and 17 links).
+inline int lmax_for(int n_links) { return n_links <= 8 ? 8 : n_links <= 9 ? 9 : n_links <= 15 ? 15 : 17; }
 
 // Plain edge validation: one warp per edge, static grid-stride over edges.
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,

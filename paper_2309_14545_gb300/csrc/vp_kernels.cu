@@ -231,10 +231,19 @@ static cudaError_t prepare(K kernel, size_t smem, int block, int *blocks_per_sm)
 // Instances: the counting variant always takes the general joint code.
 using PlainKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int32_t *,
                              const float, const long long, uint8_t *, unsigned *, unsigned long long *);
+template <int LMAX>
+static PlainKernel plain_instance(bool stats, bool simple) {
+    if (stats) return edges_plain_kernel<true, LMAX, false>;
+    return simple ? edges_plain_kernel<false, LMAX, true> : edges_plain_kernel<false, LMAX, false>;
+}
+
 static PlainKernel plain_kernel_for(int lmax, bool stats, bool simple) {
-    if (stats) return lmax <= 9 ? edges_plain_kernel<true, 9, false> : edges_plain_kernel<true, 17, false>;
-    if (lmax <= 9) return simple ? edges_plain_kernel<false, 9, true> : edges_plain_kernel<false, 9, false>;
-    return simple ? edges_plain_kernel<false, 17, true> : edges_plain_kernel<false, 17, false>;
+    switch (lmax) {
+        case 8: return plain_instance<8>(stats, simple);
+        case 9: return plain_instance<9>(stats, simple);
+        case 15: return plain_instance<15>(stats, simple);
+        default: return plain_instance<17>(stats, simple);
+    }
 }
 
 cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, size_t smem, int block, int *blocks_per_sm) {
@@ -249,17 +258,24 @@ cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const f
     return cudaGetLastError();
 }
 
+using StatesKernel = void (*)(const RobotParams, const EnvView, const float *, const long long, uint8_t *,
+                              unsigned *);
+static StatesKernel states_kernel_for(int lmax) {
+    switch (lmax) {
+        case 8: return states_kernel<8>;
+        case 9: return states_kernel<9>;
+        case 15: return states_kernel<15>;
+        default: return states_kernel<17>;
+    }
+}
+
 cudaError_t prepare_states(int lmax, size_t smem, int block, int *blocks_per_sm) {
-    return lmax <= 9 ? prepare(states_kernel<9>, smem, block, blocks_per_sm)
-                     : prepare(states_kernel<17>, smem, block, blocks_per_sm);
+    return prepare(states_kernel_for(lmax), smem, block, blocks_per_sm);
 }
 
 cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
                           unsigned *status, int grid, int block, size_t smem, cudaStream_t st) {
-    if (lmax_for(P.n_links) <= 9)
-        states_kernel<9><<<grid, block, smem, st>>>(P, env, q, N, valid, status);
-    else
-        states_kernel<17><<<grid, block, smem, st>>>(P, env, q, N, valid, status);
+    states_kernel_for(lmax_for(P.n_links))<<<grid, block, smem, st>>>(P, env, q, N, valid, status);
     return cudaGetLastError();
 }
 
