@@ -213,3 +213,37 @@ def test_argument_errors(vpmod):
     with pytest.raises(vp.VPError) as e:
         val.validate_edges(q, q, None, 0.0)
     assert e.value.status == vp.VP_ERR_ARG
+
+
+@pytest.mark.parametrize("D,parents", [
+    (9, [-1, 0, 1, 2, 1, 4, -1, 6, 3]),                                     # tree, 10 links
+    (16, [-1, 0, 1, 2, 3, 4, 2, 6, 7, -1, 9, 10, 11, 10, 13, 14]),        # 17 links
+])
+def test_tree_robot_general_axes_states_and_edges(vpmod, D, parents):
+    """Branching robots with general axes and origin rotations, prismatic
+    joints and self pairs across branches, against the oracle: the pose
+    pass restores branch-point frames, the general joint code, and the
+    17-link kernel instance."""
+    from robots_small import random_chain
+    Validator, vp = vpmod
+    rng = np.random.default_rng(100 + D)
+    r = random_chain(rng, D=D, n_spheres=60)
+    r.joint_parent = np.array(parents, dtype=np.int32)
+    links = r.sphere_link
+    cand = [(a, b) for a in range(60) for b in range(a + 1, 60) if abs(int(links[a]) - int(links[b])) >= 2]
+    r.self_pairs = np.array([cand[i] for i in rng.choice(len(cand), 80, replace=False)], dtype=np.int32)
+    env = vpgen.Env(np.array([[0.3, 0.2, 0.1, 0.15], [-0.3, 0.1, 0.2, 0.1]]),
+                    np.array([[0.0, -0.4, 0.0, 0.3, -0.2, 0.3, 0.06]]),
+                    np.array([np.concatenate([[0.1, 0.4, -0.2], np.eye(3).ravel(), [0.15, 0.1, 0.1]])]))
+    val = Validator(r, env)
+    o = oracle.Oracle(r, env)
+    q = rng.uniform(-1.5, 1.5, size=(2000, D)).astype(np.float32)
+    got, K, pinned, bad = _compare_states(val, o, q)
+    assert bad.size == 0 and 0.05 < got.mean() < 0.95
+    q0, q1 = q[:600], rng.uniform(-1.5, 1.5, size=(600, D)).astype(np.float32)
+    counts = rng.integers(2, 40, size=600).astype(np.int32)
+    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
+        v = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), 1 / 32, mode=mode).cpu().numpy()
+        cls, _ = o.classify_edges(q0, q1, counts, np.float32(1 / 32))
+        pinned = cls != 2
+        assert np.array_equal(v[pinned], (cls[pinned] == 0).astype(np.uint8)), mode
