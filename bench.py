@@ -45,7 +45,8 @@ FLOPS_TEST = {"sphere": 10, "capsule": 22, "cuboid": 26}  # squared-distance bal
 FLOPS_PAIR_COARSE = 10            # link centres already posed
 FLOPS_PAIR_FINE = 2 * FLOPS_CENTRE + 10
 WORK_NAMES = ("states", "link_centres", "coarse_sphere", "coarse_capsule", "coarse_cuboid", "fine_sphere",
-              "fine_capsule", "fine_cuboid", "pair_coarse", "pair_fine", "edges")
+              "fine_capsule", "fine_cuboid", "pair_coarse", "pair_fine", "edges", "lane_states", "lane_coarse",
+              "lane_fine", "lane_pair_fine")
 
 
 def _git_rev():
@@ -68,6 +69,20 @@ def state_flops(robot) -> float:
             canonical = np.count_nonzero(ax) == 1 and ax.max() == 1.0
             f += FLOPS_JOINT_ROT_CANONICAL if canonical else FLOPS_JOINT_ROT_GENERAL
     return f
+
+
+def lane_efficiency(work) -> dict:
+    """Live work over lane slots (every lane of a running warp, idle or not):
+    how much of the lockstep execution did work the early exit still needed."""
+    from paper_2309_14545_gb300 import vp
+    w = [float(x) for x in work]
+    coarse = w[vp.VP_WORK_COARSE_SPHERE] + w[vp.VP_WORK_COARSE_CAPSULE] + w[vp.VP_WORK_COARSE_CUBOID]
+    fine = w[vp.VP_WORK_FINE_SPHERE] + w[vp.VP_WORK_FINE_CAPSULE] + w[vp.VP_WORK_FINE_CUBOID]
+    ratio = lambda a, b: a / b if b else None
+    return {"states": ratio(w[vp.VP_WORK_STATES], w[vp.VP_WORK_LANE_STATES]),
+            "coarse": ratio(coarse, w[vp.VP_WORK_LANE_COARSE]),
+            "fine": ratio(fine, w[vp.VP_WORK_LANE_FINE]),
+            "pair_fine": ratio(w[vp.VP_WORK_PAIR_FINE], w[vp.VP_WORK_LANE_PAIR_FINE])}
 
 
 def work_flops(work, robot) -> float:
@@ -385,6 +400,7 @@ def run_native(args):
                   "evaluated_states_per_s": world * int(work[vp.VP_WORK_STATES]) / (t_max / 1000.0),
                   "covered_states_per_step": covered_all, "valid_edge_fraction": valid_frac,
                   "work_per_step": {n: int(work[i]) for i, n in enumerate(WORK_NAMES)},
+                  "lane_efficiency": lane_efficiency(work),
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
     if not args.no_compare:

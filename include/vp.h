@@ -178,8 +178,9 @@ vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const
  * or VP_MODE_BATCHED, the latter launched directly rather than from its
  * graph) with counters of the work done (VP_WORK_* indices) added into `work`
  * (device uint64 [VP_WORK_N]; the caller zeroes it).  Only lanes holding a
- * state of a live edge are counted (a lane parked on a repeated state, or in
- * a finished lane group, is not). */
+ * state of a live edge are counted (a lane parked on a repeated state, in a
+ * finished lane group or in a group that already has a collision on the
+ * current state, is not), except by the VP_WORK_LANE_* slot counters. */
 enum {
     VP_WORK_STATES = 0,     /* states posed (FK run)                          */
     VP_WORK_LINK_CENTRES,   /* link bounding-sphere centres computed          */
@@ -192,6 +193,12 @@ enum {
     VP_WORK_PAIR_COARSE,    /* link-pair bounding-sphere tests                */
     VP_WORK_PAIR_FINE,      /* sphere-pair tests                              */
     VP_WORK_EDGES_DONE,     /* edges finished                                 */
+    /* lane slots: the same work counted over every lane of a running warp,
+     * live or idle (lockstep cost; live / slots = SIMT lane efficiency)    */
+    VP_WORK_LANE_STATES,    /* poses run                                      */
+    VP_WORK_LANE_COARSE,    /* coarse primitive tests, all types              */
+    VP_WORK_LANE_FINE,      /* fine primitive tests, all types                */
+    VP_WORK_LANE_PAIR_FINE, /* sphere-pair tests                              */
     VP_WORK_N = 16
 };
 vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
@@ -225,6 +232,20 @@ vp_status vp_kernel_time(vp_ctx *ctx, int enable, float *last_ms);
  * the kernel give up at once (a way to exercise the path).  Negative or
  * non-finite values: VP_ERR_ARG. */
 vp_status vp_set_watchdog(vp_ctx *ctx, double seconds);
+
+/* The batched mode's current tiling: lanes per edge (the lane-group size,
+ * 4, 8, 16 or 32) of each edge-length bucket, as vp_autotune left it (or the
+ * defaults).  Bucket b holds edges of 2^(b+1)+1 .. 2^(b+2) states (bucket 0
+ * also 2; the last, 8, everything above 512).  Writes min(n, 9) entries into
+ * the host array lanes (n >= 0; lanes may be NULL when n == 0) and the
+ * bucket count (9) into *n_buckets when it is not NULL. */
+vp_status vp_tiling(vp_ctx *ctx, int32_t *lanes, int n, int *n_buckets);
+
+/* Set the batched mode's tiling by hand (replaces the autotuner's choice
+ * until the next vp_autotune or vp_load_robot / vp_load_env): lanes[b] for
+ * buckets b < n (n <= 9; the rest keep their value), each 4, 8, 16 or 32;
+ * VP_ERR_ARG otherwise, with nothing changed. */
+vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n);
 
 /* Synchronise `stream`, read and clear the device status word: VP_OK,
  * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are

@@ -73,6 +73,14 @@ class Validator:
     def autotune(self, q0, q1, counts=None, resolution=1.0 / 32.0, stream=None):
         vp.vp_autotune(self.ctx, q0, q1, counts, float(resolution), stream)
 
+    def tiling(self):
+        """Lanes per edge of each edge-length bucket (batched mode)."""
+        return vp.vp_tiling(self.ctx)
+
+    def set_tiling(self, lanes):
+        """Pin the batched mode's lanes per edge, bucket by bucket."""
+        vp.vp_set_tiling(self.ctx, lanes)
+
     def collision_cost(self, q, margin, grad=False, stream=None):
         cost = torch.empty(q.shape[0], dtype=torch.float32, device=self._dev())
         g = torch.empty_like(q) if grad else None

@@ -571,6 +571,29 @@ extern "C" vp_status vp_set_watchdog(vp_ctx *ctx, double seconds) {
     return VP_OK;
 }
 
+extern "C" vp_status vp_tiling(vp_ctx *ctx, int32_t *lanes, int n, int *n_buckets) {
+    if (!ctx) return VP_ERR_ARG;
+    if (n < 0 || (n > 0 && !lanes)) return fail(ctx, VP_ERR_ARG, "vp_tiling: bad output array");
+    int G[16];
+    const int nb = batched_tiling(ctx->batched, G, 16);
+    for (int b = 0; b < n && b < nb; ++b) lanes[b] = G[b];
+    if (n_buckets) *n_buckets = nb;
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n) {
+    if (!ctx) return VP_ERR_ARG;
+    if (n < 0 || n > 9 || (n > 0 && !lanes)) return fail(ctx, VP_ERR_ARG, "vp_set_tiling: n must be in [0, 9]");
+    int G[9];
+    for (int b = 0; b < n; ++b) {
+        if (lanes[b] != 4 && lanes[b] != 8 && lanes[b] != 16 && lanes[b] != 32)
+            return fail(ctx, VP_ERR_ARG, "vp_set_tiling: lanes per edge must be 4, 8, 16 or 32");
+        G[b] = lanes[b];
+    }
+    batched_set_tiling(ctx->batched, G, n);
+    return VP_OK;
+}
+
 extern "C" vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits) {
     if (!ctx) return VP_ERR_ARG;
     DeviceGuard g(ctx->device);

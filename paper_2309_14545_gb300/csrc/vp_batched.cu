@@ -11,8 +11,8 @@
 //    warp leaves a state as soon as every group has a collision or is done.
 // The three launches (plus the counter reset) are captured once into a CUDA
 // graph per buffer set and replayed.  G_b comes from the autotuner, which
-// times each bucket's sample edges with every group size and keeps the
-// fastest (cached per robot, environment and length profile).
+// times each bucket alone, at full occupancy, with every group size and keeps
+// the fastest (cached per robot, environment and length profile).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +40,7 @@ constexpr int kCtrlInts = 64;
 
 struct BatchPlan {
     int G[kNB];            // lanes per edge, per bucket
-    int edge_off[kNB + 1]; // bucket b's edges are perm[edge_off[b], edge_off[b+1]) (when !from_hist)
+    int edge_lo[kNB], edge_hi[kNB];  // bucket b's edges are perm[edge_lo[b], edge_hi[b]) (when !from_hist)
     int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
     unsigned long long watchdog_ns;  // time budget of one launch
 };
@@ -165,15 +165,15 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
             }
         } else {
             for (int b = 0; b < kNB; ++b) {
-                s_edge_lo[b] = plan.edge_off[b];
-                s_edge_hi[b] = plan.edge_off[b + 1];
+                s_edge_lo[b] = plan.edge_lo[b];
+                s_edge_hi[b] = plan.edge_hi[b];
             }
         }
         // work items in processing order: longest bucket first
         int items = 0;
         for (int b = kNB - 1; b >= 0; --b) {
             const int per = 32 / plan.G[b];
-            items += (s_edge_hi[b] - s_edge_lo[b] + per - 1) / per;
+            items += max(0, s_edge_hi[b] - s_edge_lo[b] + per - 1) / per;
             s_item_end[b] = items;
         }
         s_items = items;
@@ -204,7 +204,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         item = __shfl_sync(kFull, item, 0);
         if (item < 0 || item >= s_items) break;
         int b = kNB - 1;
-        while (item >= s_item_end[b]) --b;
+        while (b > 0 && item >= s_item_end[b]) --b;
         const int first_item = (b == kNB - 1) ? 0 : s_item_end[b + 1];
         const int G = plan.G[b];
         const int per = 32 / G;
@@ -397,6 +397,16 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_
     return e;
 }
 
+// Host mirror of offsets_from_hist.
+void offsets_host(const int *hist, int *off) {
+    int acc = 0;
+    for (int b = kNB - 1; b >= 0; --b) {
+        off[b] = acc;
+        acc += hist[b];
+    }
+    off[kNB] = acc;
+}
+
 BatchPlan plan_from(const Impl *im, unsigned long long watchdog_ns) {
     BatchPlan p;
     std::memset(&p, 0, sizeof(p));
@@ -462,20 +472,29 @@ int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *wor
     return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
 }
 
+// Tiling choice by coordinate descent on whole launches of the batch itself
+// (its first 2^23 edges at most).  The batch's own size matters: the launch
+// cannot end before its slowest work item, and an item of long edges at few
+// lanes per edge runs many rounds in series, so a tiling that is best for a
+// large batch can be worst for a small one.  The batch is bucketed once;
+// then, in order of each bucket's share of the states, every lane-group size
+// is tried for that bucket with the other buckets' choices held, timing the
+// whole launch (all buckets back to back on one queue).  A bucket moves off
+// its current size only for a 1% gain, so noise does not churn the choice;
+// passes repeat (at most three) until none moves.
 int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     Impl *im = impl_of(st);
-    const int64_t S = std::min<int64_t>(a.E, 1 << 17);  // tuning sample: the first edges
-    int rc = ensure_capacity(im, S, msg);
-    if (rc) return rc;
     size_t smem = 0;
     int grid = 0;
-    rc = prepare_kernel(a, &smem, &grid, msg);
+    int rc = prepare_kernel(a, &smem, &grid, msg);
+    if (rc) return rc;
+    const int64_t S = std::min<int64_t>(a.E, int64_t{1} << 23);
+    rc = ensure_capacity(im, S, msg);
     if (rc) return rc;
     cudaStream_t s = a.stream;
     uint8_t *tv = nullptr;
     cudaError_t e = cudaMalloc(&tv, S);
     if (e != cudaSuccess) return set_err(msg, "cudaMalloc tuning output", e);
-    // bucket the sample once
     const unsigned nb = static_cast<unsigned>((S + 255) / 256);
     e = cudaMemsetAsync(im->ctrl, 0, kCtrlInts * sizeof(int), s);
     if (e == cudaSuccess) {
@@ -498,7 +517,8 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     key.nc = a.env->nc;
     key.nb = a.env->nb;
     key.sms = a.num_sms;
-    for (int b = 0; b < kNB; ++b) key.profile.push_back(hist[b] == 0 ? 0 : 1 + (20 * hist[b]) / static_cast<int>(S));
+    for (int b = 0; b < kNB; ++b)
+        key.profile.push_back(hist[b] == 0 ? 0 : 1 + static_cast<int>((20 * static_cast<int64_t>(hist[b])) / S));
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
@@ -510,61 +530,80 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
             return 0;
         }
     }
-    int off[kNB + 1];
+    BatchPlan p;
+    std::memset(&p, 0, sizeof(p));
     {
-        int acc = 0;
-        for (int b = kNB - 1; b >= 0; --b) {
-            off[b] = acc;
-            acc += hist[b];
+        int off[kNB + 1];
+        offsets_host(hist, off);
+        for (int b = 0; b < kNB; ++b) {
+            p.edge_lo[b] = off[b];
+            p.edge_hi[b] = off[b] + hist[b];
         }
-        off[kNB] = acc;
     }
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    const int options[4] = {4, 8, 16, 32};
-    for (int b = 0; b < kNB && e == cudaSuccess; ++b) {
-        if (hist[b] < 64) continue;  // too few to time: keep the default
+    p.from_hist = 0;
+    p.watchdog_ns = st.watchdog_ns;
+    const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+    for (int b = 0; b < kNB; ++b) p.G[b] = defaults[b];
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    // one timing: the best of two runs of the whole sample
+    auto time_plan = [&](float *ms_out) {
         float best = 1e30f;
-        int best_g = im->G[b];
-        for (int G : options) {
-            BatchPlan p;
-            std::memset(&p, 0, sizeof(p));
-            for (int c = 0; c < kNB; ++c) {
-                p.G[c] = G;
-                p.edge_off[c] = 0;
-            }
-            p.edge_off[kNB] = 0;
-            // only bucket b: every other bucket empty
-            for (int c = 0; c <= kNB; ++c) p.edge_off[c] = (c <= b) ? off[b] : off[b] + hist[b];
-            p.from_hist = 0;
-            p.watchdog_ns = st.watchdog_ns;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
-                if (e != cudaSuccess) break;
-                cudaEventRecord(t0, s);
-                batched_kernel_for(*a.robot, false)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1,
-                                                                               im->perm, p, tv, a.status, im->ctrl,
-                                                                               nullptr);
-                cudaEventRecord(t1, s);
-                e = cudaEventSynchronize(t1);
-                if (e == cudaSuccess) e = cudaGetLastError();
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, t0, t1);
-                if (rep > 0) ms_min = std::min(ms_min, ms);
-            }
-            if (ms_min < best) {
-                best = ms_min;
-                best_g = G;
-            }
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
+            if (e != cudaSuccess) break;
+            cudaEventRecord(t0, s);
+            batched_kernel_for(*a.robot, false)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm,
+                                                                           p, tv, a.status, im->ctrl, nullptr);
+            cudaEventRecord(t1, s);
+            e = cudaEventSynchronize(t1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            float ms = 0.f;
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, t0, t1);
+            best = std::min(best, ms);
         }
-        im->G[b] = best_g;
+        *ms_out = best;
+    };
+    // buckets by their (approximate) share of the sample's states, largest first
+    int order[kNB];
+    for (int b = 0; b < kNB; ++b) order[b] = b;
+    std::stable_sort(order, order + kNB, [&](int x, int y) {
+        return static_cast<double>(hist[x]) * (1 << x) > static_cast<double>(hist[y]) * (1 << y);
+    });
+    float cur = 0.f;
+    time_plan(&cur);  // warm-up
+    time_plan(&cur);
+    const int options[4] = {4, 8, 16, 32};
+    bool moved = true;
+    for (int pass = 0; pass < 3 && moved && e == cudaSuccess; ++pass) {
+        moved = false;
+        for (int oi = 0; oi < kNB && e == cudaSuccess; ++oi) {
+            const int b = order[oi];
+            if (hist[b] < 64) continue;  // too few to matter: keep the default
+            const int keep = p.G[b];
+            int best_g = keep;
+            float best = cur;
+            for (int G : options) {
+                if (G == keep || e != cudaSuccess) continue;
+                p.G[b] = G;
+                float ms = 0.f;
+                time_plan(&ms);
+                if (ms < 0.99f * best) {
+                    best = ms;
+                    best_g = G;
+                }
+            }
+            p.G[b] = best_g;
+            moved = moved || best_g != keep;
+            cur = best;
+        }
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
     cudaFree(tv);
     if (e != cudaSuccess) return set_err(msg, "tuning runs", e);
+    for (int b = 0; b < kNB; ++b) im->G[b] = p.G[b];
     im->tuned = true;
     drop_graph(im);
     {
@@ -593,6 +632,13 @@ void batched_release(BatchedState &st) {
     if (im->cap_stream) cudaStreamDestroy(im->cap_stream);
     delete im;
     st.impl = nullptr;
+}
+
+void batched_set_tiling(BatchedState &st, const int *G, int n) {
+    Impl *im = impl_of(st);
+    for (int b = 0; b < n && b < kNB; ++b) im->G[b] = G[b];
+    im->tuned = true;
+    drop_graph(im);
 }
 
 int batched_tiling(const BatchedState &st, int *G, int n) {

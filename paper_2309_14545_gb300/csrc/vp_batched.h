@@ -39,5 +39,7 @@ void batched_invalidate(BatchedState &st);
 void batched_release(BatchedState &st);
 // Lanes per edge chosen for each length bucket; returns the bucket count.
 int batched_tiling(const BatchedState &st, int *G, int n);
+// Replace the first n buckets' lanes per edge (values already checked).
+void batched_set_tiling(BatchedState &st, const int *G, int n);
 
 }  // namespace vp

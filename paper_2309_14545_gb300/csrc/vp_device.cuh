@@ -298,6 +298,10 @@ struct WorkRef {
     __device__ __forceinline__ void add(int i, uint32_t n) const {
         if (STATS && real) w->v[i] += n;
     }
+    // lane-slot counters: every lane of the running warp, live or not
+    __device__ __forceinline__ void slot(int i, uint32_t n) const {
+        if (STATS) w->v[i] += n;
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -332,22 +336,27 @@ enum : int { kStopAny = 0, kStopAll = 1, kStopGroups = 2 };
 
 struct Ctl {
     unsigned gmask;  // lanes of this lane's group (kStopGroups)
-    bool idle;       // this lane's group is finished and must not drive the warp
+    bool idle;       // this lane must not drive the warp: its group is finished
+                     // with its edge, or (set while checking) already has a
+                     // collision on the current state
 };
 
+// The warp's stop vote after a fine test; marks a lane whose group (or, for
+// kStopAll, the lane itself) has collided as idle for the rest of the state.
 template <int MODE>
-__device__ __forceinline__ bool group_stop(const Ctl &c, bool col) {
+__device__ __forceinline__ bool group_stop(Ctl &c, bool col) {
     if (MODE == kStopAny) return __any_sync(kFull, col);
-    if (MODE == kStopAll) return __all_sync(kFull, col);
+    if (MODE == kStopAll) {
+        c.idle = c.idle || col;
+        return __all_sync(kFull, col);
+    }
     const bool gcol = (__ballot_sync(kFull, col) & c.gmask) != 0u;
-    return __all_sync(kFull, gcol || c.idle);
+    c.idle = c.idle || gcol;
+    return __all_sync(kFull, c.idle);
 }
 
-// A lane's vote for extra (fine) work: idle groups never ask for it.
-template <int MODE>
-__device__ __forceinline__ bool wants(const Ctl &c, bool v) {
-    return MODE == kStopGroups ? (v && !c.idle) : v;
-}
+// A lane's vote for extra (fine) work: idle lanes never ask for it.
+__device__ __forceinline__ bool wants(const Ctl &c, bool v) { return v && !c.idle; }
 
 // ---------------------------------------------------------------------------
 // the check of one configuration
@@ -381,7 +390,7 @@ struct Kind<2> {
 // decision.
 template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE>
 __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, int n, const float *cx,
-                                          const float *cy, const float *cz, const Stash &stash, const Ctl &ctl,
+                                          const float *cy, const float *cz, const Stash &stash, Ctl &ctl,
                                           bool &col, const WorkRef<STATS> &w) {
     using K = Kind<KIND>;
     const unsigned lmask = P.link_mask;
@@ -398,8 +407,9 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 #pragma unroll
         for (int l = 0; l < LMAX; ++l)
             bits |= static_cast<unsigned>(K::hit(make_float3(cx[l], cy[l], cz[l]), P.links[l].bs.w, o)) << l;
-        w.add(K::kCoarse, __popc(lmask));
-        if (MODE == kStopGroups && ctl.idle) bits = 0;
+        w.slot(VP_WORK_LANE_COARSE, __popc(lmask));
+        if (!ctl.idle) w.add(K::kCoarse, __popc(lmask));
+        if (ctl.idle) bits = 0;
         unsigned any = __reduce_or_sync(kFull, bits);
         while (any) {
             const int l = __ffs(any) - 1;
@@ -407,7 +417,8 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
             const LinkC &L = P.links[l];
             Fr f;
             recompute_frame_cached<SIMPLE>(P, l, stash, f);
-            w.add(K::kFine, L.s1 - L.s0);
+            w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
+            if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
             const bool h = (bits >> l) & 1u;
 #pragma unroll 1
             for (int s = L.s0; s < L.s1; ++s) {
@@ -435,10 +446,12 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 // Returns this lane's collision flag; the warp stops early per MODE.
 template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
 __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
-                                               const Stash &stash, const Ctl &ctl, const WorkRef<STATS> &w) {
+                                               const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w) {
     bool col = false;
+    Ctl ctl = ctl_in;
     const int D = P.n_joints;
     w.add(VP_WORK_STATES, 1);
+    w.slot(VP_WORK_LANE_STATES, 1);
     // 1. pose
     {
         Fr f;
@@ -475,8 +488,8 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
             const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
             const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
-            w.add(VP_WORK_PAIR_COARSE, 1);
-            if (__any_sync(kFull, wants<MODE>(ctl, h))) {
+            if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
+            if (__any_sync(kFull, wants(ctl, h))) {
                 if (G.lb != lb_cached) {
                     recompute_frame_cached<SIMPLE>(P, G.lb, stash, fb);
                     lb_cached = G.lb;
@@ -485,7 +498,8 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
                     recompute_frame_cached<SIMPLE>(P, G.la, stash, fa);
                     la_cached = G.la;
                 }
-                w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+                w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
+                if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
 #pragma unroll 1
                 for (int p = G.p0; p < G.p1; ++p) {
                     const PairC pr = P.pairs[p];

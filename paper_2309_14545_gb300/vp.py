@@ -27,14 +27,15 @@ VP_NOALLOC_MAX_ENV_BYTES = 64 * 1024
 VP_MAX_STEPS = 16777216
 (VP_WORK_STATES, VP_WORK_LINK_CENTRES, VP_WORK_COARSE_SPHERE, VP_WORK_COARSE_CAPSULE, VP_WORK_COARSE_CUBOID,
  VP_WORK_FINE_SPHERE, VP_WORK_FINE_CAPSULE, VP_WORK_FINE_CUBOID, VP_WORK_PAIR_COARSE, VP_WORK_PAIR_FINE,
- VP_WORK_EDGES_DONE) = range(11)
+ VP_WORK_EDGES_DONE, VP_WORK_LANE_STATES, VP_WORK_LANE_COARSE, VP_WORK_LANE_FINE,
+ VP_WORK_LANE_PAIR_FINE) = range(15)
 VP_WORK_N = 16
 
 #: Every symbol include/vp.h declares.
 EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load_env", "vp_fk_spheres",
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
-           "vp_kernel_time", "vp_set_watchdog")
+           "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling")
 
 
 class VPError(RuntimeError):
@@ -77,6 +78,8 @@ def _load_lib():
         "vp_validate_edges_noalloc": (U, [P, P, P, P, P, F, I64, P, P, C.c_char_p, I32]),
         "vp_kernel_time": (U, [P, U, C.POINTER(C.c_float)]),
         "vp_set_watchdog": (U, [P, C.c_double]),
+        "vp_tiling": (U, [P, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_int)]),
+        "vp_set_tiling": (U, [P, C.POINTER(C.c_int32), C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +232,21 @@ def vp_kernel_time(ctx, enable=True):
 
 def vp_set_watchdog(ctx, seconds):
     _check(ctx, lib.vp_set_watchdog(ctx, C.c_double(seconds)))
+
+
+def vp_tiling(ctx):
+    """Lanes per edge of each edge-length bucket of the batched mode."""
+    arr = (C.c_int32 * 16)()
+    nb = C.c_int(0)
+    _check(ctx, lib.vp_tiling(ctx, arr, 16, C.byref(nb)))
+    return [int(arr[b]) for b in range(min(nb.value, 16))]
+
+
+def vp_set_tiling(ctx, lanes):
+    """Set lanes per edge for the first len(lanes) buckets (each 4, 8, 16 or 32)."""
+    lanes = [int(x) for x in lanes]
+    arr = (C.c_int32 * max(1, len(lanes)))(*lanes)
+    _check(ctx, lib.vp_set_tiling(ctx, arr, len(lanes)))
 
 
 def vp_sync_status(ctx, stream=None):

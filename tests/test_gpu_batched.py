@@ -115,6 +115,34 @@ def test_batched_work_counters(vpmod):
     assert work[vp.VP_WORK_EDGES_DONE] == 20_000
     assert work[vp.VP_WORK_STATES] >= 20_000 * 2 * 0  # at least one state per edge that is posed
     assert work[vp.VP_WORK_STATES] <= int(w.counts.astype(np.int64).sum())
+    # lane slots: every lane of a running warp, so whole warps, and at least the live work
+    coarse = work[[vp.VP_WORK_COARSE_SPHERE, vp.VP_WORK_COARSE_CAPSULE, vp.VP_WORK_COARSE_CUBOID]].sum()
+    fine = work[[vp.VP_WORK_FINE_SPHERE, vp.VP_WORK_FINE_CAPSULE, vp.VP_WORK_FINE_CUBOID]].sum()
+    for slot, live in ((vp.VP_WORK_LANE_STATES, work[vp.VP_WORK_STATES]), (vp.VP_WORK_LANE_COARSE, coarse),
+                       (vp.VP_WORK_LANE_FINE, fine), (vp.VP_WORK_LANE_PAIR_FINE, work[vp.VP_WORK_PAIR_FINE])):
+        assert work[slot] % 32 == 0 and work[slot] >= live > 0
+
+
+def test_tiling_defaults_then_tuned(vpmod):
+    Validator, vp = vpmod
+    w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=100_000)
+    val = Validator(w.robot, w.env)
+    assert val.tiling() == [4, 8, 16, 32, 32, 32, 32, 32, 32]
+    val.autotune(_cuda(w.q0), _cuda(w.q1), _cuda(w.counts), float(w.res))
+    t = val.tiling()
+    assert len(t) == 9 and set(t) <= {4, 8, 16, 32}
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    want = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    for lanes in ([32] * 9, [4] * 9, [8, 16]):
+        val.set_tiling(lanes)
+        assert val.tiling()[:len(lanes)] == lanes
+        got = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+        assert np.array_equal(got, want)
+    for bad in ([3], [64], [4] * 10):
+        with pytest.raises(vp.VPError):
+            val.set_tiling(bad)
+    assert val.tiling()[:2] == [8, 16]
+    val.close()
 
 
 def test_kernel_timing_hook(vpmod):
