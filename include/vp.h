@@ -120,6 +120,8 @@ typedef struct {
  *   capsules [n][7]  segment end p0, end p1, radius
  *   cuboids  [n][15] centre, R (3x3 row-major; column i = box axis i in the
  *                    world frame), half-extents
+ * Packed for the device (with each primitive's world box): 48 bytes per
+ * sphere, 64 per capsule, 96 per cuboid.
  */
 typedef struct {
     int32_t n_spheres;
@@ -199,6 +201,8 @@ enum {
     VP_WORK_LANE_COARSE,    /* coarse primitive tests, all types              */
     VP_WORK_LANE_FINE,      /* fine primitive tests, all types                */
     VP_WORK_LANE_PAIR_FINE, /* sphere-pair tests                              */
+    VP_WORK_BOX_TESTS,      /* (link, primitive) world-box overlap tests that
+                             * cull coarse tests (one per pair per warp)      */
     VP_WORK_N = 16
 };
 vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,

@@ -311,6 +311,7 @@ struct EnvSm {
     const float4 *sph;  // [ns]
     const float4 *cap;  // [2 nc]
     const float4 *box;  // [4 nb]
+    const float4 *bb_sph, *bb_cap, *bb_box;  // world boxes [2 n] of each kind
     int ns, nc, nb;
     int kind_order;     // kinds in visiting order, 4 bits each
 };
@@ -320,6 +321,9 @@ __device__ __forceinline__ EnvSm env_in_smem(const float4 *sm, const EnvView &en
     e.sph = sm;
     e.cap = sm + env.ns;
     e.box = sm + env.ns + 2 * env.nc;
+    e.bb_sph = e.box + 4 * env.nb;
+    e.bb_cap = e.bb_sph + 2 * env.ns;
+    e.bb_box = e.bb_cap + 2 * env.nc;
     e.ns = env.ns;
     e.nc = env.nc;
     e.nb = env.nb;
@@ -384,48 +388,106 @@ struct Kind<2> {
     }
 };
 
+// Warp-wide boxes of the links: for each link, the axis-aligned box of its
+// bounding sphere over the warp's live lanes (empty when none is live).  Lane
+// t keeps the box of link t mod LMAX, the link it tests in box_cull below.
+struct LinkBox {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ float warp_min(float v) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+template <int LMAX>
+__device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const Stash &stash, bool live) {
+    const float inf = __int_as_float(0x7f800000);
+    const int my_l = (threadIdx.x & 31) % LMAX;
+    LinkBox b{inf, inf, inf, -inf, -inf, -inf};
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+        if (!((P.link_mask >> l) & 1u)) continue;  // warp-uniform
+        const float r = P.links[l].bs.w;
+        const float3 c = stash.centre(l);
+        const float lx = warp_min(live ? c.x - r : inf), ly = warp_min(live ? c.y - r : inf),
+                    lz = warp_min(live ? c.z - r : inf);
+        const float hx = warp_max(live ? c.x + r : -inf), hy = warp_max(live ? c.y + r : -inf),
+                    hz = warp_max(live ? c.z + r : -inf);
+        if (my_l == l) b = LinkBox{lx, ly, lz, hx, hy, hz};
+    }
+    return b;
+}
+
 // Every primitive of one kind (largest first) against every link's bounding
-// sphere at once -- independent tests for the scheduler -- then the fine
-// spheres of each link some lane's coarse test hit.  Returns the warp's stop
-// decision.
+// sphere, then the fine spheres of each link some lane's coarse test hit.
+// Primitives go in batches of 32 / LMAX: lane t compares the world box of
+// primitive t / LMAX of the batch with link t mod LMAX's warp-wide box, and
+// a ballot leaves the (link, primitive) pairs whose boxes overlap; only those
+// take the exact ball test.  The cull is conservative (the primitive boxes
+// carry a rounding margin), so the verdicts are those of testing every pair.
+// Returns the warp's stop decision.
 template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE>
-__device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, int n, const float *cx,
-                                          const float *cy, const float *cz, const Stash &stash, Ctl &ctl,
-                                          bool &col, const WorkRef<STATS> &w) {
+__device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, const float4 *boxes, int n,
+                                          const LinkBox &lb, const Stash &stash, Ctl &ctl, bool &col,
+                                          const WorkRef<STATS> &w) {
     using K = Kind<KIND>;
-    const unsigned lmask = P.link_mask;
+    constexpr int PB = 32 / LMAX > 0 ? 32 / LMAX : 1;  // primitives per batch
+    constexpr unsigned kLinks = (1u << LMAX) - 1u;
+    const int lane = threadIdx.x & 31;
+    const int my_l = lane % LMAX, my_p = lane / LMAX;
+    const bool my_on = my_p < PB && ((P.link_mask >> my_l) & 1u);
 #pragma unroll 1
-    for (int k = 0; k < n; ++k) {
-        float4 o[K::kWords];
+    for (int k0 = 0; k0 < n; k0 += PB) {
+        const int kb = k0 + my_p;
+        bool ov = false;
+        if (my_on && kb < n) {
+            const float4 lo = boxes[2 * kb], hi = boxes[2 * kb + 1];
+            ov = (lo.x <= lb.hx) & (hi.x >= lb.lx) & (lo.y <= lb.hy) & (hi.y >= lb.ly) & (lo.z <= lb.hz) &
+                 (hi.z >= lb.lz);
+            w.slot(VP_WORK_BOX_TESTS, 1);
+        }
+        unsigned m = __ballot_sync(kFull, ov);
+        while (m) {  // warp-uniform: primitives of the batch with an overlapping link
+            const int p = (__ffs(m) - 1) / LMAX;
+            const unsigned lm = (m >> (p * LMAX)) & kLinks;
+            m &= ~(kLinks << (p * LMAX));
+            const int k = k0 + p;
+            float4 o[K::kWords];
 #pragma unroll
-        for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
-        unsigned bits = 0;
-        // no per-link branch: a link without spheres (or past the robot's
-        // last link) sits at 1e30, where every test fails (its squared
-        // distance overflows to +inf; for a cuboid some |a_i . c| >= 1e30
-        // since the box axes span space)
-#pragma unroll
-        for (int l = 0; l < LMAX; ++l)
-            bits |= static_cast<unsigned>(K::hit(make_float3(cx[l], cy[l], cz[l]), P.links[l].bs.w, o)) << l;
-        w.slot(VP_WORK_LANE_COARSE, __popc(lmask));
-        if (!ctl.idle) w.add(K::kCoarse, __popc(lmask));
-        if (ctl.idle) bits = 0;
-        unsigned any = __reduce_or_sync(kFull, bits);
-        while (any) {
-            const int l = __ffs(any) - 1;
-            any &= any - 1;
-            const LinkC &L = P.links[l];
-            Fr f;
-            recompute_frame_cached<SIMPLE>(P, l, stash, f);
-            w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
-            if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
-            const bool h = (bits >> l) & 1u;
+            for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
+            unsigned bits = 0;
 #pragma unroll 1
-            for (int s = L.s0; s < L.s1; ++s) {
-                const float4 sp = P.spheres[s];
-                col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, o);
+            for (unsigned t = lm; t; t &= t - 1) {  // the links that survived the cull
+                const int l = __ffs(t) - 1;
+                bits |= static_cast<unsigned>(K::hit(stash.centre(l), P.links[l].bs.w, o)) << l;
             }
-            if (group_stop<MODE>(ctl, col)) return true;
+            w.slot(VP_WORK_LANE_COARSE, __popc(lm));
+            if (!ctl.idle) w.add(K::kCoarse, __popc(lm));
+            if (ctl.idle) bits = 0;
+            unsigned any = __reduce_or_sync(kFull, bits);
+            while (any) {
+                const int l = __ffs(any) - 1;
+                any &= any - 1;
+                const LinkC &L = P.links[l];
+                Fr f;
+                recompute_frame_cached<SIMPLE>(P, l, stash, f);
+                w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
+                if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
+                const bool h = (bits >> l) & 1u;
+#pragma unroll 1
+                for (int s = L.s0; s < L.s1; ++s) {
+                    const float4 sp = P.spheres[s];
+                    col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, o);
+                }
+                if (group_stop<MODE>(ctl, col)) return true;
+            }
         }
     }
     return false;
@@ -437,12 +499,14 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 //      sphere in the per-lane stash;
 //   2. self pairs: link-pair bounding-sphere test, then the sphere pairs of
 //      the link pairs some lane's coarse test hit;
-//   3. primitives, kind by kind, each against every link's bounding sphere,
-//      then fine spheres where a coarse test hit.
+//   3. primitives, kind by kind, each against every link's bounding sphere
+//      (pairs first culled by warp-wide boxes, see prim_pass), then fine
+//      spheres where a coarse test hit.
 // Frames needed by fine tests are recomputed from the kept (sin, cos).  The
 // order of checks is chosen for early exit: a colliding configuration is
 // most often found by a self pair or a large primitive; it does not change
-// the verdict.  LMAX bounds the link count (centres held in registers).
+// the verdict.  LMAX bounds the link count (a compile-time bound for the
+// per-link loops and the cull's lane layout).
 // Returns this lane's collision flag; the warp stops early per MODE.
 template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
 __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
@@ -514,27 +578,17 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             }
         }
     }
-    // 3. primitives against every link
-    float cx[LMAX], cy[LMAX], cz[LMAX];
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-        cx[l] = cy[l] = cz[l] = 1e30f;  // far away: no primitive is within reach
-        if ((P.link_mask >> l) & 1u) {
-            const float3 c = stash.centre(l);
-            cx[l] = c.x;
-            cy[l] = c.y;
-            cz[l] = c.z;
-        }
-    }
+    // 3. primitives against every link, culled by warp-wide link boxes
+    const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
     for (int ki = 0; ki < 3; ++ki) {
         const int kind = (env.kind_order >> (4 * ki)) & 15;
         bool stop;
         if (kind == 0)
-            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.ns, cx, cy, cz, stash, ctl, col, w);
+            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, ctl, col, w);
         else if (kind == 1)
-            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.nc, cx, cy, cz, stash, ctl, col, w);
+            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, ctl, col, w);
         else
-            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.nb, cx, cy, cz, stash, ctl, col, w);
+            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, ctl, col, w);
         if (stop) return col;
     }
     return col;

@@ -34,9 +34,34 @@ int env_packed_float4(const vp_env_desc *e, size_t *n4, std::string *msg) {
         *msg = "too many primitives";
         return 2;
     }
-    *n4 = static_cast<size_t>(ns) + 2 * static_cast<size_t>(nc) + 4 * static_cast<size_t>(nb);
+    *n4 = 3 * static_cast<size_t>(ns) + 4 * static_cast<size_t>(nc) + 6 * static_cast<size_t>(nb);
     return 0;
 }
+
+namespace {
+
+// float nearest to x on the side away from the box (outward rounding)
+float round_down(double x) {
+    float f = static_cast<float>(x);
+    if (static_cast<double>(f) > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+float round_up(double x) {
+    float f = static_cast<float>(x);
+    if (static_cast<double>(f) < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+// A primitive's world box [lo, hi] grown by the rounding margin, as floats.
+void put_box(float4 *out, const double lo[3], const double hi[3]) {
+    double m = 0.0;
+    for (int a = 0; a < 3; ++a) m = std::max(m, std::max(std::fabs(lo[a]), std::fabs(hi[a])));
+    const double g = kBoxMarginAbs + kBoxMarginRel * (1.0 + m);
+    out[0] = float4{round_down(lo[0] - g), round_down(lo[1] - g), round_down(lo[2] - g), 0.f};
+    out[1] = float4{round_up(hi[0] + g), round_up(hi[1] + g), round_up(hi[2] + g), 0.f};
+}
+
+}  // namespace
 
 int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view, std::string *msg) {
     size_t n4 = 0;
@@ -104,6 +129,37 @@ int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view
             out[k++] = float4{float(ax[0]), float(ax[1]), float(ax[2]), float(-off)};
         }
         out[k++] = float4{float(p[12]), float(p[13]), float(p[14]), 0.f};
+    }
+    // world boxes, same kinds and order
+    for (const auto &it : os) {
+        const double *p = e->spheres + 4 * it.second;
+        const double lo[3] = {p[0] - p[3], p[1] - p[3], p[2] - p[3]};
+        const double hi[3] = {p[0] + p[3], p[1] + p[3], p[2] + p[3]};
+        put_box(out + k, lo, hi);
+        k += 2;
+    }
+    for (const auto &it : oc) {
+        const double *p = e->capsules + 7 * it.second;
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(p[a], p[3 + a]) - p[6];
+            hi[a] = std::max(p[a], p[3 + a]) + p[6];
+        }
+        put_box(out + k, lo, hi);
+        k += 2;
+    }
+    for (const auto &it : ob) {
+        const double *p = e->cuboids + 15 * it.second;
+        const double *c = p, *R = p + 3, *h = p + 12;
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {  // world axis a: |R_a0| h0 + |R_a1| h1 + |R_a2| h2
+            const double ext = std::fabs(R[3 * a]) * h[0] + std::fabs(R[3 * a + 1]) * h[1] +
+                               std::fabs(R[3 * a + 2]) * h[2];
+            lo[a] = c[a] - ext;
+            hi[a] = c[a] + ext;
+        }
+        put_box(out + k, lo, hi);
+        k += 2;
     }
     // kinds visited in order of their largest member
     const double top[3] = {os.empty() ? -1.0 : os[0].first, oc.empty() ? -1.0 : oc[0].first,

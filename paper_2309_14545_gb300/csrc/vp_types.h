@@ -79,14 +79,24 @@ struct RobotParams {
 
 // Environment layout (float4 units): spheres [ns] (c, r); capsules [2 nc]
 // ((p0, r), (u = p1 - p0, 1/|u|^2)); cuboids [4 nb] ((a_i, -a_i . c) for the
-// three box axes a_i, then (h, 0)).  Each kind is stored largest bounding
-// radius first; kind_order lists the kinds (0 sphere, 1 capsule, 2 cuboid;
-// 4 bits each) in order of their largest member.
+// three box axes a_i, then (h, 0)); then the world axis-aligned box of every
+// primitive [2 (ns + nc + nb)] ((lo, 0), (hi, 0)), kinds in the same order
+// (spheres, capsules, cuboids), each box grown outward by a margin that
+// covers the float rounding of the exact tests (kBoxMargin*).  Each kind is
+// stored largest bounding radius first; kind_order lists the kinds (0
+// sphere, 1 capsule, 2 cuboid; 4 bits each) in order of their largest member.
 struct EnvView {
     const float4 *data;
     int ns, nc, nb;
     int n_float4;    // total float4 count
     int kind_order;  // visiting order of the kinds
 };
+
+// Primitive box margin: kBoxMarginAbs + kBoxMarginRel * (1 + max |coordinate|)
+// metres.  An fp32 ball test that reports contact implies a true distance
+// below the radius plus a few ulp of the coordinates (about 1e-6 m per metre
+// of coordinate); the margin is ten times that and more.
+constexpr double kBoxMarginAbs = 1e-4;
+constexpr double kBoxMarginRel = 1e-5;
 
 }  // namespace vp

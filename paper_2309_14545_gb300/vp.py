@@ -28,7 +28,7 @@ VP_MAX_STEPS = 16777216
 (VP_WORK_STATES, VP_WORK_LINK_CENTRES, VP_WORK_COARSE_SPHERE, VP_WORK_COARSE_CAPSULE, VP_WORK_COARSE_CUBOID,
  VP_WORK_FINE_SPHERE, VP_WORK_FINE_CAPSULE, VP_WORK_FINE_CUBOID, VP_WORK_PAIR_COARSE, VP_WORK_PAIR_FINE,
  VP_WORK_EDGES_DONE, VP_WORK_LANE_STATES, VP_WORK_LANE_COARSE, VP_WORK_LANE_FINE,
- VP_WORK_LANE_PAIR_FINE) = range(15)
+ VP_WORK_LANE_PAIR_FINE, VP_WORK_BOX_TESTS) = range(16)
 VP_WORK_N = 16
 
 #: Every symbol include/vp.h declares.

@@ -54,7 +54,7 @@ def test_noalloc_matches_plain_on_consecutive_calls(vpmod):
 def test_noalloc_rejects_an_environment_beyond_the_scratch(vpmod):
     Validator, vp = vpmod
     w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=64)
-    n = vp.VP_NOALLOC_MAX_ENV_BYTES // 64 + 1  # cuboids pack to 64 bytes each
+    n = vp.VP_NOALLOC_MAX_ENV_BYTES // 96 + 1  # cuboids pack to 96 bytes each
     big = vpgen.Env(np.zeros((0, 4)), np.zeros((0, 7)),
                     np.tile(np.concatenate([[5.0, 5, 5], np.eye(3).ravel(), [0.1, 0.1, 0.1]]), (n, 1)))
     q0, q1 = torch.from_numpy(w.q0).cuda(), torch.from_numpy(w.q1).cuda()
