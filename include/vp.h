@@ -251,6 +251,17 @@ vp_status vp_tiling(vp_ctx *ctx, int32_t *lanes, int n, int *n_buckets);
  * VP_ERR_ARG otherwise, with nothing changed. */
 vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n);
 
+/* Screening rounds of the batched mode.  Its first launch gives each edge
+ * to a lane group for at most `rounds` raked rounds (lanes-per-edge states
+ * each); edges still undecided then go to a second launch that spreads each
+ * of them over whole warps, so a long collision-free edge does not keep one
+ * lane group busy while the rest of the GPU idles.  0 = no limit (edges are
+ * finished in the first launch).  vp_autotune chooses it along with the
+ * tiling; vp_set_screen_rounds pins it (rounds >= 0, else VP_ERR_ARG) until
+ * the next vp_autotune or load.  The verdicts do not depend on it. */
+vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds);
+vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
+
 /* Synchronise `stream`, read and clear the device status word: VP_OK,
  * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are
  * returned in *bits when bits != NULL. */

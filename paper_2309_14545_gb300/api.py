@@ -81,6 +81,13 @@ class Validator:
         """Pin the batched mode's lanes per edge, bucket by bucket."""
         vp.vp_set_tiling(self.ctx, lanes)
 
+    def screen_rounds(self):
+        """Screening rounds of the batched mode (0: single phase)."""
+        return vp.vp_screen_rounds(self.ctx)
+
+    def set_screen_rounds(self, rounds):
+        vp.vp_set_screen_rounds(self.ctx, rounds)
+
     def collision_cost(self, q, margin, grad=False, stream=None):
         cost = torch.empty(q.shape[0], dtype=torch.float32, device=self._dev())
         g = torch.empty_like(q) if grad else None

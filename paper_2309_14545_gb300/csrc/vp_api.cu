@@ -370,16 +370,34 @@ extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
 
 namespace {
 
-// Largest block (128, 64 or 32 threads) whose shared memory fits the
-// opt-in limit; returns false if none does.
-bool plan_block(vp_ctx *ctx, int *block, size_t *smem) {
+// Launch shape of a plain-path validation kernel: the largest block (128,
+// 64 or 32 threads) whose shared memory fits the opt-in limit, and where the
+// environment lives -- in each block's shared memory, unless copying it
+// there lowers the blocks per SM (then the kernel reads it in place, through
+// L1; its loads are warp-uniform).  prep(smem, block, &bps) sets the
+// kernel's shared-memory limit and reports its occupancy; it is called for
+// the in-place size first and the staged size last, so the limit ends at the
+// larger (prep also names the placement, for kernels with an instance per
+// placement).  Returns false if no block fits.
+template <class Prep>
+bool plan_launch(vp_ctx *ctx, Prep prep, EnvView *view, int *block, size_t *smem, int *bps, cudaError_t *err) {
+    *err = cudaSuccess;
     for (int b : {128, 64, 32}) {
-        const size_t s = smem_bytes(ctx->env, ctx->robot.n_links, b);
-        if (s <= ctx->smem_optin) {
-            *block = b;
-            *smem = s;
-            return true;
-        }
+        EnvView v0 = ctx->env, v1 = ctx->env;
+        v0.staged = 0;
+        v1.staged = 1;
+        const size_t s0 = smem_bytes(v0, ctx->robot.n_links, b), s1 = smem_bytes(v1, ctx->robot.n_links, b);
+        if (s0 > ctx->smem_optin) continue;
+        int b0 = 0, b1 = 0;
+        *err = prep(s0, b, false, &b0);
+        if (*err == cudaSuccess && s1 <= ctx->smem_optin) *err = prep(s1, b, true, &b1);
+        if (*err != cudaSuccess) return true;
+        const bool staged = b1 >= 1 && b1 >= b0;
+        *view = staged ? v1 : v0;
+        *block = b;
+        *smem = staged ? s1 : s0;
+        *bps = staged ? b1 : b0;
+        return true;
     }
     return false;
 }
@@ -412,16 +430,20 @@ extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, 
     if (n == 0) return VP_OK;
     if (!q || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
-    int block = 0;
+    int block = 0, bps = 0;
     size_t smem = 0;
-    if (!plan_block(ctx, &block, &smem))
-        return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
-    int bps = 0;
-    cudaError_t e = prepare_states(lmax_for(ctx->robot.n_links), smem, block, &bps);
+    EnvView view;
+    cudaError_t e = cudaSuccess;
+    const int lmax = lmax_for(ctx->robot.n_links);
+    if (!plan_launch(
+            ctx, [lmax](size_t sm, int b, bool, int *o) { return prepare_states(lmax, sm, b, o); }, &view, &block, &smem,
+            &bps, &e))
+        return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
-        e = launch_states(ctx->robot, ctx->env, q, n, valid, ctx->status, static_cast<int>(grid), block, smem,
+        const int64_t grid =
+            std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(std::max(bps, 1)) * ctx->num_sms));
+        e = launch_states(ctx->robot, view, q, n, valid, ctx->status, static_cast<int>(grid), block, smem,
                           static_cast<cudaStream_t>(stream));
     }
     return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_states");
@@ -470,28 +492,35 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
         if (rc == 0) return VP_OK;
         return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "batched: %s", msg.c_str());
     }
-    int block = 0;
+    int block = 0, bps = 0;
     size_t smem = 0;
-    if (!plan_block(ctx, &block, &smem))
-        return fail(ctx, VP_ERR_CAPACITY, "environment and frame stash exceed shared memory");
-    int bps = 0;
-    cudaError_t e = prepare_edges_plain(work != nullptr, lmax_for(ctx->robot.n_links), ctx->robot.simple != 0, smem,
-                                        block, &bps);
+    EnvView view;
+    cudaError_t e = cudaSuccess;
+    const bool stats = work != nullptr, simple = ctx->robot.simple != 0;
+    const int lmax = lmax_for(ctx->robot.n_links);
+    if (!plan_launch(
+            ctx,
+            [stats, lmax, simple](size_t sm, int b, bool staged, int *o) {
+                return prepare_edges_plain(stats, lmax, simple, staged, sm, b, o);
+            },
+            &view, &block, &smem, &bps, &e))
+        return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges (prepare)");
     if (bps < 1) return fail(ctx, VP_ERR_CAPACITY, "plain edge kernel cannot be resident");
     const int wpb = block / 32;
     if (mode == VP_MODE_PER_EDGE && !work) {
         const int D = ctx->robot.n_joints;
+        const size_t smem32 = smem_bytes(view, ctx->robot.n_links, 32);
         for (int64_t i = 0; i < n_edges && e == cudaSuccess; ++i)
-            e = launch_edges_plain(ctx->robot, ctx->env, q0 + i * D, q1 + i * D, counts ? counts + i : nullptr,
-                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem_bytes(ctx->env, ctx->robot.n_links, 32), st);
+            e = launch_edges_plain(ctx->robot, view, q0 + i * D, q1 + i * D, counts ? counts + i : nullptr,
+                                   resolution, 1, valid + i, ctx->status, nullptr, 1, 32, smem32, st);
         return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges (per edge)");
     }
     const int64_t need = (n_edges + wpb - 1) / wpb;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(bps) * ctx->num_sms));
     if (timed) e = cudaEventRecord(ctx->ev_start, st);
     if (e == cudaSuccess)
-        e = launch_edges_plain(ctx->robot, ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
+        e = launch_edges_plain(ctx->robot, view, q0, q1, counts, resolution, n_edges, valid, ctx->status,
                                reinterpret_cast<unsigned long long *>(work), static_cast<int>(grid), block, smem, st);
     if (e == cudaSuccess && timed) e = cudaEventRecord(ctx->ev_stop, st);
     return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges");
@@ -591,6 +620,19 @@ extern "C" vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n) {
         G[b] = lanes[b];
     }
     batched_set_tiling(ctx->batched, G, n);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds) {
+    if (!ctx) return VP_ERR_ARG;
+    if (rounds < 0) return fail(ctx, VP_ERR_ARG, "vp_set_screen_rounds: rounds must be >= 0");
+    batched_set_screen_rounds(ctx->batched, rounds);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds) {
+    if (!ctx || !rounds) return VP_ERR_ARG;
+    *rounds = batched_screen_rounds(ctx->batched);
     return VP_OK;
 }
 

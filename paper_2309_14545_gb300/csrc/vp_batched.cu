@@ -24,53 +24,11 @@
 #include <vector>
 
 #include "vp_batched.h"
-#include "vp_device.cuh"
-#include "vp_internal.h"
+#include "vp_validate.cuh"
 
 namespace vp {
 
 namespace {
-
-constexpr int kNB = 9;           // length buckets
-constexpr int kBlock = 128;      // threads per block of the persistent kernel
-constexpr int kCtrlHist = 0;     // ctrl[0..8]   edges per bucket
-constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
-constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
-constexpr int kCtrlInts = 64;
-
-struct BatchPlan {
-    int G[kNB];            // lanes per edge, per bucket
-    int edge_lo[kNB], edge_hi[kNB];  // bucket b's edges are perm[edge_lo[b], edge_hi[b]) (when !from_hist)
-    int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
-    unsigned long long watchdog_ns;  // time budget of one launch
-};
-
-__host__ __device__ __forceinline__ int bucket_of(int k) {
-    // ceil(log2 k) - 2, clamped: [2,4] -> 0, [5,8] -> 1, ..., [257,512] -> 7, > 512 -> 8
-    int c = 0;
-    unsigned v = static_cast<unsigned>(k - 1);
-    while (v) {
-        ++c;
-        v >>= 1;
-    }
-    return min(max(c - 2, 0), kNB - 1);
-}
-
-// Exclusive offsets of the buckets in processing order (longest first).
-__device__ __forceinline__ void offsets_from_hist(const int *hist, int *off) {
-    int acc = 0;
-    for (int b = kNB - 1; b >= 0; --b) {
-        off[b] = acc;
-        acc += hist[b];
-    }
-    off[kNB] = acc;  // total; off[b] + hist[b] is bucket b's end
-}
-
-__device__ __forceinline__ int count_from_dmax_b(float dmax, float res) {
-    const float steps = ceilf(__fdiv_rn(dmax, res));
-    if (!(steps <= static_cast<float>(VP_MAX_STEPS))) return -1;
-    return max(2, static_cast<int>(steps) + 1);
-}
 
 __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, const float *__restrict__ q1,
                                     const int32_t *__restrict__ counts, const float res, const long long E,
@@ -96,7 +54,7 @@ __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, c
                 k = -1;
             }
         } else if (fin) {
-            k = count_from_dmax_b(dmax, res);
+            k = count_from_dmax(dmax, res);
             if (k < 0) atomicOr(status, VP_DEVERR_LENGTH);
         }
         if (!fin) k = -1;
@@ -132,157 +90,17 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
     if (b >= 0) perm[off[b] + base[b] + r] = make_int2(static_cast<int>(e), k);
 }
 
-// Persistent validation of bucketed edges; see the file comment.  STATS adds
-// the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
-template <bool STATS, int LMAX, bool SIMPLE>
-__global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
-    const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
-    const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
-    unsigned *status, int *ctrl, unsigned long long *work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_edge_lo[kNB], s_edge_hi[kNB], s_item_end[kNB];
-    __shared__ int s_items;
-    size_t off = static_cast<size_t>(env.n_float4) * 16;
-    float4 *env_sm = reinterpret_cast<float4 *>(smem);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
-    off += 16;
-    float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
-    off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
-    Stash stash;
-    stash.frames = nullptr;
-    stash.centres = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_links) * kCentreFloats * kBlock * sizeof(float);
-    stash.motion = reinterpret_cast<float *>(smem + off);
-    stash.stride = kBlock;
+BatchedKernel batched_kernel_for(const RobotParams &P, bool stats, bool staged) {
+    return kernel_set(lmax_for(P.n_links)).batched[stats][P.simple != 0][staged];
+}
 
-    if (threadIdx.x == 0) {
-        int eo[kNB + 1];
-        if (plan.from_hist) {
-            offsets_from_hist(ctrl + kCtrlHist, eo);
-            for (int b = 0; b < kNB; ++b) {
-                s_edge_lo[b] = eo[b];
-                s_edge_hi[b] = eo[b] + ctrl[kCtrlHist + b];
-            }
-        } else {
-            for (int b = 0; b < kNB; ++b) {
-                s_edge_lo[b] = plan.edge_lo[b];
-                s_edge_hi[b] = plan.edge_hi[b];
-            }
-        }
-        // work items in processing order: longest bucket first
-        int items = 0;
-        for (int b = kNB - 1; b >= 0; --b) {
-            const int per = 32 / plan.G[b];
-            items += max(0, s_edge_hi[b] - s_edge_lo[b] + per - 1) / per;
-            s_item_end[b] = items;
-        }
-        s_items = items;
-    }
-    __syncthreads();
-    if (!stage_env(env_sm, env.data, env.n_float4, bar, status)) return;
-    const EnvSm es = env_in_smem(env_sm, env);
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int D = P.n_joints;
-    float *wbuf = gbuf + wib * 8 * 32;
-    const uint64_t t_start = global_ns();
-    Work wk;
-    if (STATS) {
-#pragma unroll
-        for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
-    }
-
-    while (true) {
-        int item = 0;
-        if (lane == 0) {
-            if (global_ns() - t_start >= plan.watchdog_ns) {
-                atomicOr(status, VP_DEVERR_TIMEOUT);
-                item = -1;
-            } else {
-                item = atomicAdd(&ctrl[kCtrlQueue], 1);
-            }
-        }
-        item = __shfl_sync(kFull, item, 0);
-        if (item < 0 || item >= s_items) break;
-        int b = kNB - 1;
-        while (b > 0 && item >= s_item_end[b]) --b;
-        const int first_item = (b == kNB - 1) ? 0 : s_item_end[b + 1];
-        const int G = plan.G[b];
-        const int per = 32 / G;
-        const int g = lane / G, j = lane - g * G;
-        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
-        const int slot = s_edge_lo[b] + (item - first_item) * per + g;
-        const bool has_edge = g < per && slot < s_edge_hi[b];
-        const int2 ek = has_edge ? perm[slot] : make_int2(0, 2);
-        const int e = ek.x, k = ek.y;
-        float *gq0 = wbuf + g * 32, *gdq = gq0 + 16;
-        __syncwarp();
-        if (has_edge) {
-            for (int d = j; d < D; d += G) {
-                const float a = q0[static_cast<long long>(e) * D + d];
-                gq0[d] = a;
-                gdq[d] = q1[static_cast<long long>(e) * D + d] - a;
-            }
-        } else {
-            for (int d = j; d < 16; d += G) {
-                gq0[d] = 0.f;
-                gdq[d] = 0.f;
-            }
-        }
-        __syncwarp();
-        const int R = (k + G - 1) / G;
-        const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
-        const int R_max = __reduce_max_sync(kFull, has_edge ? R : 0);
-        bool done = !has_edge;
-        for (int r = 0; r < R_max; ++r) {
-            int i = j * R + r;
-            const WorkRef<STATS> w{&wk, !done && i < k};
-            if (i >= k) i = k - 1;
-            const float t = static_cast<float>(i) * inv;
-            const bool c = pose_and_check<kStopGroups, STATS, LMAX, SIMPLE>(
-                P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w);
-            const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
-            if (!done && (gcol || r == R - 1)) {
-                if (j == 0) {
-                    valid[e] = gcol ? 0 : 1;
-                    if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
-                }
-                done = true;
-            }
-            if (__all_sync(kFull, done)) break;
-        }
-        if constexpr (STATS) {
-#pragma unroll
-            for (int c = 0; c < VP_WORK_N; ++c) {
-                const unsigned sum = __reduce_add_sync(kFull, wk.v[c]);
-                if (lane == 0 && sum) atomicAdd(work + c, static_cast<unsigned long long>(sum));
-                wk.v[c] = 0;
-            }
-        }
-    }
+SurvivorsKernel survivors_kernel_for(const RobotParams &P, bool stats, bool staged) {
+    return kernel_set(lmax_for(P.n_links)).survivors[stats][P.simple != 0][staged];
 }
 
 size_t batched_smem(const EnvView &env, const RobotParams &P) {
-    return static_cast<size_t>(env.n_float4) * 16 + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
+    return env_smem_bytes(env) + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
            static_cast<size_t>(P.n_links * kCentreFloats + P.n_joints * 2) * kBlock * sizeof(float);
-}
-
-// The kernel instance for this robot's link count and counting mode.
-using BatchedKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int2 *,
-                               const BatchPlan, uint8_t *, unsigned *, int *, unsigned long long *);
-template <int LMAX>
-BatchedKernel batched_instance(bool stats, bool simple) {
-    if (stats) return edges_batched_kernel<true, LMAX, false>;
-    return simple ? edges_batched_kernel<false, LMAX, true> : edges_batched_kernel<false, LMAX, false>;
-}
-
-BatchedKernel batched_kernel_for(const RobotParams &P, bool stats) {
-    const bool simple = P.simple != 0;
-    switch (lmax_for(P.n_links)) {
-        case 8: return batched_instance<8>(stats, simple);
-        case 9: return batched_instance<9>(stats, simple);
-        case 15: return batched_instance<15>(stats, simple);
-        default: return batched_instance<17>(stats, simple);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -303,6 +121,7 @@ std::map<TuneKey, std::vector<int>> g_tune_cache;
 struct Impl {
     int32_t *kbuf = nullptr;  // state count per edge (-1: answered in the bucketing pass)
     int2 *perm = nullptr;     // (edge, count) bucket by bucket, longest bucket first
+    int2 *surv = nullptr;     // (edge, count) of the edges left to the second phase
     int *ctrl = nullptr;
     int64_t cap = 0;
     cudaStream_t cap_stream = nullptr;
@@ -314,6 +133,7 @@ struct Impl {
     int64_t k_E = -1;
     float k_res = 0.f;
     int G[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
+    int screen_rounds = kDefaultScreenRounds;
     bool tuned = false;
 };
 
@@ -346,30 +166,55 @@ int ensure_capacity(Impl *im, int64_t E, std::string *msg) {
     drop_graph(im);
     if (im->kbuf) cudaFree(im->kbuf);
     if (im->perm) cudaFree(im->perm);
+    if (im->surv) cudaFree(im->surv);
     im->kbuf = nullptr;
     im->perm = nullptr;
+    im->surv = nullptr;
     im->cap = 0;
     const int64_t n = std::max<int64_t>(E, 1 << 16);
     cudaError_t e = cudaMalloc(&im->kbuf, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&im->perm, n * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&im->surv, n * sizeof(int2));
     if (e != cudaSuccess) return set_err(msg, "cudaMalloc scratch", e);
     im->cap = n;
     return 0;
 }
 
-int prepare_kernel(const BatchedArgs &a, size_t *smem, int *grid, std::string *msg) {
-    *smem = batched_smem(*a.env, *a.robot);
-    if (*smem > a.smem_optin) {
-        *msg = "environment and frame stash exceed shared memory";
+// Shared memory, grid and environment placement of the persistent kernels:
+// the environment goes into each block's shared memory unless that lowers
+// the blocks per SM (then it is read in place, through L1).
+int prepare_kernel(const BatchedArgs &a, EnvView *view, size_t *smem, int *grid, std::string *msg) {
+    EnvView vin = *a.env, vst = *a.env;
+    vin.staged = 0;
+    vst.staged = 1;
+    const size_t m_in = batched_smem(vin, *a.robot), m_st = batched_smem(vst, *a.robot);
+    if (m_in > a.smem_optin) {
+        *msg = "frame stash exceeds shared memory";
         return 1;
     }
-    const BatchedKernel k0 = batched_kernel_for(*a.robot, false), k1 = batched_kernel_for(*a.robot, true);
-    cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(*smem));
+    const size_t m_max = m_st <= a.smem_optin ? m_st : m_in;
+    cudaError_t e = cudaSuccess;
+    for (int stats = 0; stats < 2; ++stats)
+        for (int staged = 0; staged < 2; ++staged) {
+            const void *k[2] = {reinterpret_cast<const void *>(batched_kernel_for(*a.robot, stats, staged)),
+                                reinterpret_cast<const void *>(survivors_kernel_for(*a.robot, stats, staged))};
+            const size_t m = staged ? m_max : m_in;
+            for (const void *f : k)
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m));
+        }
+    int b_in = 0, b_st = 0;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(*smem));
-    int bps = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k0, kBlock, *smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_in, batched_kernel_for(*a.robot, false, false), kBlock,
+                                                          m_in);
+    if (e == cudaSuccess && m_st <= a.smem_optin)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_st, batched_kernel_for(*a.robot, false, true), kBlock,
+                                                          m_st);
     if (e != cudaSuccess) return set_err(msg, "batched kernel attributes", e);
+    const bool staged = b_st >= 1 && b_st >= b_in;
+    *view = staged ? vst : vin;
+    *smem = staged ? m_st : m_in;
+    const int bps = staged ? b_st : b_in;
     if (bps < 1) {
         *msg = "batched kernel cannot be resident";
         return 1;
@@ -379,8 +224,8 @@ int prepare_kernel(const BatchedArgs &a, size_t *smem, int *grid, std::string *m
 }
 
 // Enqueue the whole pipeline on stream s (also used under capture).
-cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_t smem, int grid, cudaStream_t s,
-                    uint8_t *valid, unsigned long long *work = nullptr) {
+cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const BatchPlan &plan, size_t smem, int grid,
+                    cudaStream_t s, uint8_t *valid, unsigned long long *work = nullptr) {
     const int D = a.robot->n_joints;
     cudaError_t e = cudaMemsetAsync(im->ctrl, 0, kCtrlInts * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -390,8 +235,13 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const BatchPlan &plan, size_
     // external event-record nodes, so the events time the kernel when replayed from the graph
     if (a.ev_start) e = cudaEventRecordWithFlags(a.ev_start, s, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    batched_kernel_for(*a.robot, work != nullptr)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm,
-                                                                            plan, valid, a.status, im->ctrl, work);
+    batched_kernel_for(*a.robot, work != nullptr, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
+                                                                            plan, valid, a.status, im->ctrl, im->surv,
+                                                                            work);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    survivors_kernel_for(*a.robot, work != nullptr, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+                                                                              plan, valid, a.status, im->ctrl, work);
     e = cudaGetLastError();
     if (e == cudaSuccess && a.ev_stop) e = cudaEventRecordWithFlags(a.ev_stop, s, cudaEventRecordExternal);
     return e;
@@ -412,6 +262,7 @@ BatchPlan plan_from(const Impl *im, unsigned long long watchdog_ns) {
     std::memset(&p, 0, sizeof(p));
     for (int b = 0; b < kNB; ++b) p.G[b] = im->G[b];
     p.from_hist = 1;
+    p.screen_rounds = im->screen_rounds;
     p.watchdog_ns = watchdog_ns;
     return p;
 }
@@ -424,7 +275,8 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     if (rc) return rc;
     size_t smem = 0;
     int grid = 0;
-    rc = prepare_kernel(a, &smem, &grid, msg);
+    EnvView view;
+    rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
     const bool same = im->exec && im->k_q0 == a.q0 && im->k_q1 == a.q1 && im->k_counts == a.counts &&
                       im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res && im->k_ev == a.ev_start &&
@@ -434,7 +286,7 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(im->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return set_err(msg, "begin capture", e);
-        cudaError_t e2 = enqueue(im, a, plan_from(im, st.watchdog_ns), smem, grid, im->cap_stream, a.valid);
+        cudaError_t e2 = enqueue(im, a, view, plan_from(im, st.watchdog_ns), smem, grid, im->cap_stream, a.valid);
         e = cudaStreamEndCapture(im->cap_stream, &graph);
         if (e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -466,9 +318,10 @@ int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *wor
     if (rc) return rc;
     size_t smem = 0;
     int grid = 0;
-    rc = prepare_kernel(a, &smem, &grid, msg);
+    EnvView view;
+    rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
-    const cudaError_t e = enqueue(im, a, plan_from(im, st.watchdog_ns), smem, grid, a.stream, a.valid, work);
+    const cudaError_t e = enqueue(im, a, view, plan_from(im, st.watchdog_ns), smem, grid, a.stream, a.valid, work);
     return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
 }
 
@@ -486,7 +339,8 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     Impl *im = impl_of(st);
     size_t smem = 0;
     int grid = 0;
-    int rc = prepare_kernel(a, &smem, &grid, msg);
+    EnvView view;
+    int rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
     const int64_t S = std::min<int64_t>(a.E, int64_t{1} << 23);
     rc = ensure_capacity(im, S, msg);
@@ -524,6 +378,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             for (int b = 0; b < kNB; ++b) im->G[b] = it->second[b];
+            im->screen_rounds = it->second[kNB];
             im->tuned = true;
             drop_graph(im);
             cudaFree(tv);
@@ -544,6 +399,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     p.watchdog_ns = st.watchdog_ns;
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) p.G[b] = defaults[b];
+    p.screen_rounds = kDefaultScreenRounds;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -551,11 +407,14 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     auto time_plan = [&](float *ms_out) {
         float best = 1e30f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, sizeof(int), s);
+            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, 3 * sizeof(int), s);  // both queues, survivor count
             if (e != cudaSuccess) break;
             cudaEventRecord(t0, s);
-            batched_kernel_for(*a.robot, false)<<<grid, kBlock, smem, s>>>(*a.robot, *a.env, a.q0, a.q1, im->perm,
-                                                                           p, tv, a.status, im->ctrl, nullptr);
+            batched_kernel_for(*a.robot, false, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
+                                                                           p, tv, a.status, im->ctrl, im->surv,
+                                                                           nullptr);
+            survivors_kernel_for(*a.robot, false, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+                                                                             p, tv, a.status, im->ctrl, nullptr);
             cudaEventRecord(t1, s);
             e = cudaEventSynchronize(t1);
             if (e == cudaSuccess) e = cudaGetLastError();
@@ -574,6 +433,25 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     float cur = 0.f;
     time_plan(&cur);  // warm-up
     time_plan(&cur);
+    // screening rounds (0: no second phase), with the other choices held
+    auto tune_screen = [&]() {
+        const int keep = p.screen_rounds;
+        int best_r = keep;
+        float best = cur;
+        for (int R : {1, 2, 4, 8, 0}) {
+            if (R == keep || e != cudaSuccess) continue;
+            p.screen_rounds = R;
+            float ms = 0.f;
+            time_plan(&ms);
+            if (ms < 0.99f * best) {
+                best = ms;
+                best_r = R;
+            }
+        }
+        p.screen_rounds = best_r;
+        cur = best;
+    };
+    tune_screen();
     const int options[4] = {4, 8, 16, 32};
     bool moved = true;
     for (int pass = 0; pass < 3 && moved && e == cudaSuccess; ++pass) {
@@ -599,16 +477,20 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
             cur = best;
         }
     }
+    if (e == cudaSuccess) tune_screen();
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(tv);
     if (e != cudaSuccess) return set_err(msg, "tuning runs", e);
     for (int b = 0; b < kNB; ++b) im->G[b] = p.G[b];
+    im->screen_rounds = p.screen_rounds;
     im->tuned = true;
     drop_graph(im);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = std::vector<int>(im->G, im->G + kNB);
+        std::vector<int> v(im->G, im->G + kNB);
+        v.push_back(im->screen_rounds);
+        g_tune_cache[key] = v;
     }
     return 0;
 }
@@ -620,6 +502,7 @@ void batched_invalidate(BatchedState &st) {
     im->tuned = false;
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) im->G[b] = defaults[b];
+    im->screen_rounds = kDefaultScreenRounds;
 }
 
 void batched_release(BatchedState &st) {
@@ -628,10 +511,23 @@ void batched_release(BatchedState &st) {
     drop_graph(im);
     if (im->kbuf) cudaFree(im->kbuf);
     if (im->perm) cudaFree(im->perm);
+    if (im->surv) cudaFree(im->surv);
     if (im->ctrl) cudaFree(im->ctrl);
     if (im->cap_stream) cudaStreamDestroy(im->cap_stream);
     delete im;
     st.impl = nullptr;
+}
+
+void batched_set_screen_rounds(BatchedState &st, int rounds) {
+    Impl *im = impl_of(st);
+    im->screen_rounds = rounds;
+    im->tuned = true;
+    drop_graph(im);
+}
+
+int batched_screen_rounds(const BatchedState &st) {
+    const Impl *im = static_cast<const Impl *>(st.impl);
+    return im ? im->screen_rounds : kDefaultScreenRounds;
 }
 
 void batched_set_tiling(BatchedState &st, const int *G, int n) {

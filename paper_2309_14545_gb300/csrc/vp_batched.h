@@ -6,9 +6,55 @@
 
 #include <string>
 
+#include "vp_internal.h"
 #include "vp_types.h"
 
 namespace vp {
+
+constexpr int kNB = 9;           // length buckets
+constexpr int kBlock = 128;      // threads per block of the persistent kernel
+constexpr int kCtrlHist = 0;     // ctrl[0..8]   edges per bucket
+constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
+constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
+constexpr int kCtrlSurv = 33;    // ctrl[33]     edges left to the second phase
+constexpr int kCtrlQueue2 = 34;  // ctrl[34]     second-phase work-item counter
+constexpr int kCtrlInts = 64;
+constexpr int kSplit = 16;       // second-phase work items per edge
+constexpr int kDefaultScreenRounds = 4;
+
+struct BatchPlan {
+    int G[kNB];            // lanes per edge, per bucket
+    int edge_lo[kNB], edge_hi[kNB];  // bucket b's edges are perm[edge_lo[b], edge_hi[b]) (when !from_hist)
+    int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
+    int screen_rounds;     // rounds a lane group spends on an edge before handing it on (0: no limit)
+    unsigned long long watchdog_ns;  // time budget of one launch
+};
+
+// Kernel entry points, by link bound, counting mode, joint code and
+// environment placement.
+using PlainKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int32_t *, float, long long,
+                             uint8_t *, unsigned *, unsigned long long *);
+using BatchedKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
+                               uint8_t *, unsigned *, int *, int2 *, unsigned long long *);
+using SurvivorsKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
+                                 uint8_t *, unsigned *, int *, unsigned long long *);
+struct KernelSet {
+    PlainKernel plain[2][2][2];          // [stats][simple][staged]
+    BatchedKernel batched[2][2][2];
+    SurvivorsKernel survivors[2][2][2];
+};
+const KernelSet &kernel_set_l8();
+const KernelSet &kernel_set_l9();
+const KernelSet &kernel_set_l15();
+const KernelSet &kernel_set_l17();
+inline const KernelSet &kernel_set(int lmax) {
+    switch (lmax) {
+        case 8: return kernel_set_l8();
+        case 9: return kernel_set_l9();
+        case 15: return kernel_set_l15();
+        default: return kernel_set_l17();
+    }
+}
 
 struct BatchedArgs {
     const RobotParams *robot;
@@ -41,5 +87,8 @@ void batched_release(BatchedState &st);
 int batched_tiling(const BatchedState &st, int *G, int n);
 // Replace the first n buckets' lanes per edge (values already checked).
 void batched_set_tiling(BatchedState &st, const int *G, int n);
+// Screening rounds of the first phase (0: no limit, no second phase).
+void batched_set_screen_rounds(BatchedState &st, int rounds);
+int batched_screen_rounds(const BatchedState &st);
 
 }  // namespace vp

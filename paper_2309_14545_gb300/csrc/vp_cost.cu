@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
                                                    float *__restrict__ cost, float *__restrict__ grad,
                                                    unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t off = static_cast<size_t>(env.n_float4) * 16;
+    size_t off = env_smem_bytes(env);
     float4 *env_sm = reinterpret_cast<float4 *>(smem);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
     off += 16;
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
     stash.centres = nullptr;
     stash.motion = nullptr;
     stash.stride = static_cast<int>(blockDim.x);
-    if (!stage_env(env_sm, env.data, env.n_float4, bar, status)) return;
-    const EnvSm es = env_in_smem(env_sm, env);
+    if (!stage_env(env_sm, env, bar, status)) return;
+    const EnvSm es = env_views_rt(env_sm, env);
     const int D = P.n_joints;
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -218,29 +218,40 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
 
 int cost_launch(const RobotParams &P, const EnvView &env, const float *q, int64_t n, float margin, float *cost,
                 float *grad, unsigned *status, int num_sms, size_t smem_optin, cudaStream_t st, std::string *msg) {
-    int block = 0;
+    // largest block that fits; the environment in shared memory unless that
+    // lowers the blocks per SM (then read in place, through L1)
+    int block = 0, bps = 0;
     size_t smem = 0;
+    EnvView view = env;
+    cudaError_t e = cudaSuccess;
     for (int b : {128, 64, 32}) {
-        const size_t s = static_cast<size_t>(env.n_float4) * 16 + 16 +
-                         static_cast<size_t>(P.n_links * kLinkFloats + P.n_slots * kFrameFloats) * b * sizeof(float);
-        if (s <= smem_optin) {
-            block = b;
-            smem = s;
-            break;
-        }
+        const size_t rest = 16 + static_cast<size_t>(P.n_links * kLinkFloats + P.n_slots * kFrameFloats) * b *
+                                     sizeof(float);
+        EnvView vst = env;
+        vst.staged = 1;
+        const size_t m_st = env_smem_bytes(vst) + rest;
+        if (rest > smem_optin) continue;
+        const size_t m_max = m_st <= smem_optin ? m_st : rest;
+        e = cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m_max));
+        int b_in = 0, b_st = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_in, cost_kernel, b, rest);
+        if (e == cudaSuccess && m_st <= smem_optin)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_st, cost_kernel, b, m_st);
+        if (e != cudaSuccess) break;
+        view.staged = (b_st >= 1 && b_st >= b_in) ? 1 : 0;
+        smem = view.staged ? m_st : rest;
+        bps = view.staged ? b_st : b_in;
+        block = b;
+        break;
     }
-    if (!block) {
-        *msg = "environment and per-link adjoint storage exceed shared memory";
+    if (e == cudaSuccess && !block) {
+        *msg = "per-link adjoint storage exceeds shared memory";
         return 1;
     }
-    cudaError_t e = cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    int bps = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cost_kernel, block, smem);
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(std::max(bps, 1)) * num_sms));
-        cost_kernel<<<static_cast<unsigned>(grid), block, smem, st>>>(P, env, q, n, margin, cost, grad, status);
+        cost_kernel<<<static_cast<unsigned>(grid), block, smem, st>>>(P, view, q, n, margin, cost, grad, status);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -182,10 +182,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 // cp.async.bulk completing on an mbarrier.  Every thread of the block calls
 // this.  The wait is bounded (about one second); on expiry the status word
 // gets VP_DEVERR_TIMEOUT and false is returned (the block must not use dst).
-__device__ __forceinline__ bool stage_env(float4 *dst, const float4 *src, int n_float4, uint64_t *bar,
-                                          unsigned *status) {
-    if (n_float4 == 0) return true;
-    const uint32_t bytes = static_cast<uint32_t>(n_float4) * 16u;
+__device__ __forceinline__ bool stage_env(float4 *dst, const EnvView &env, uint64_t *bar, unsigned *status) {
+    if (!env.staged || env.n_float4 == 0) return true;  // read in place
+    const float4 *src = env.data;
+    const uint32_t bytes = static_cast<uint32_t>(env.n_float4) * 16u;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -316,11 +316,15 @@ struct EnvSm {
     int kind_order;     // kinds in visiting order, 4 bits each
 };
 
-__device__ __forceinline__ EnvSm env_in_smem(const float4 *sm, const EnvView &env) {
+// Views of the environment: the block's shared copy (STAGED), or the device
+// buffer itself.  A compile-time choice keeps the loads' address space known.
+template <bool STAGED>
+__device__ __forceinline__ EnvSm env_views(const float4 *sm, const EnvView &env) {
     EnvSm e;
-    e.sph = sm;
-    e.cap = sm + env.ns;
-    e.box = sm + env.ns + 2 * env.nc;
+    const float4 *base = STAGED ? sm : env.data;
+    e.sph = base;
+    e.cap = base + env.ns;
+    e.box = base + env.ns + 2 * env.nc;
     e.bb_sph = e.box + 4 * env.nb;
     e.bb_cap = e.bb_sph + 2 * env.ns;
     e.bb_box = e.bb_cap + 2 * env.nc;
@@ -329,6 +333,11 @@ __device__ __forceinline__ EnvSm env_in_smem(const float4 *sm, const EnvView &en
     e.nb = env.nb;
     e.kind_order = env.kind_order;
     return e;
+}
+
+// The same, placement chosen at run time (generic loads).
+__device__ __forceinline__ EnvSm env_views_rt(const float4 *sm, const EnvView &env) {
+    return env.staged ? env_views<true>(sm, env) : env_views<false>(sm, env);
 }
 
 // Early-exit rules.  Every vote spans the full warp; a warp may hold one

@@ -35,7 +35,8 @@ inline int lmax_for(int n_links) { return n_links <= 8 ? 8 : n_links <= 9 ? 9 : 
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, size_t smem, int block, int *blocks_per_sm);
+cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, bool staged, size_t smem, int block,
+                                int *blocks_per_sm);
 
 cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
                           unsigned *status, int grid, int block, size_t smem, cudaStream_t st);

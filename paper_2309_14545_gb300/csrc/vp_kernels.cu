@@ -2,139 +2,14 @@
 // states), state validation, FK sphere centres and edge state counts.
 #include <cuda_runtime.h>
 
-#include "vp_device.cuh"
-#include "vp_internal.h"
+#include "vp_validate.cuh"
 
 namespace vp {
 
 size_t smem_bytes(const EnvView &env, int n_links, int block) {
     const size_t warps = static_cast<size_t>((block + 31) / 32);
-    return static_cast<size_t>(env.n_float4) * 16 + 16 + warps * 32 * sizeof(float) +
+    return env_smem_bytes(env) + 16 + warps * 32 * sizeof(float) +
            static_cast<size_t>(n_links * kCentreFloats + (n_links - 1) * 2) * block * sizeof(float);
-}
-
-// State count of an edge from its largest joint displacement (float32, IEEE
-// division): max(2, ceil(dmax / res) + 1); -1 past VP_MAX_STEPS.
-__device__ __forceinline__ int count_from_dmax(float dmax, float res) {
-    const float steps = ceilf(__fdiv_rn(dmax, res));
-    if (!(steps <= static_cast<float>(VP_MAX_STEPS))) return -1;
-    return max(2, static_cast<int>(steps) + 1);
-}
-
-struct SmemCarve {
-    float4 *env;
-    uint64_t *bar;
-    float *warp_buf;
-    Stash stash;
-};
-
-__device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &env, const RobotParams &P) {
-    SmemCarve c;
-    size_t off = static_cast<size_t>(env.n_float4) * 16;
-    c.env = reinterpret_cast<float4 *>(smem);
-    c.bar = reinterpret_cast<uint64_t *>(smem + off);
-    off += 16;
-    c.warp_buf = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>((blockDim.x + 31) / 32) * 32 * sizeof(float);
-    c.stash.frames = nullptr;
-    c.stash.centres = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_links) * kCentreFloats * blockDim.x * sizeof(float);
-    c.stash.motion = reinterpret_cast<float *>(smem + off);
-    c.stash.stride = static_cast<int>(blockDim.x);
-    return c;
-}
-
-template <bool STATS>
-__device__ __forceinline__ void flush_work(Work &wk, unsigned long long *work, int lane) {
-    if constexpr (STATS) {
-#pragma unroll
-        for (int i = 0; i < VP_WORK_N; ++i) {
-            const unsigned s = __reduce_add_sync(kFull, wk.v[i]);
-            if (lane == 0 && s) atomicAdd(work + i, static_cast<unsigned long long>(s));
-            wk.v[i] = 0;
-        }
-    }
-}
-
-// One warp per edge.  Lane j of the warp checks states j*R + r in round r
-// (R = ceil(k/32) rounds): the rake of Sec. III-D, 32 spread states per
-// round.  Lanes past the end park on the last state.
-template <bool STATS, int LMAX, bool SIMPLE>
-__global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
-                                                          const float *__restrict__ q0, const float *__restrict__ q1,
-                                                          const int32_t *__restrict__ counts, const float res,
-                                                          const long long E, uint8_t *__restrict__ valid,
-                                                          unsigned *status, unsigned long long *work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const SmemCarve sc = carve(smem, env, P);
-    if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
-    const EnvSm es = env_in_smem(sc.env, env);
-    const Stash &stash = sc.stash;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    float *wq0 = sc.warp_buf + wib * 32;
-    float *wdq = wq0 + 16;
-    const int D = P.n_joints;
-    Work wk;
-    if (STATS) {
-#pragma unroll
-        for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
-    }
-    for (long long e = static_cast<long long>(blockIdx.x) * wpb + wib; e < E;
-         e += static_cast<long long>(gridDim.x) * wpb) {
-        float a = 0.f, b = 0.f;
-        if (lane < D) {
-            a = q0[e * D + lane];
-            b = q1[e * D + lane];
-        }
-        const bool fin = isfinite(a) && isfinite(b);
-        const float d = b - a;
-        const bool all_fin = __all_sync(kFull, fin);
-        const float dmax = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(fin ? fabsf(d) : 0.f)));
-        if (lane < 16) {
-            wq0[lane] = a;
-            wdq[lane] = d;
-        }
-        __syncwarp();
-        int k = 2;
-        bool ok = all_fin;
-        if (counts != nullptr) {
-            k = counts[e];
-            if (k < 2) {
-                ok = false;
-                if (lane == 0) atomicOr(status, VP_DEVERR_COUNT);
-            }
-        } else if (ok) {
-            k = count_from_dmax(dmax, res);
-            if (k < 0) {
-                ok = false;
-                if (lane == 0) atomicOr(status, VP_DEVERR_LENGTH);
-            }
-        }
-        bool collided = !ok;
-        if (ok) {
-            const int R = (k + 31) >> 5;
-            const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
-            for (int r = 0; r < R; ++r) {
-                int i = lane * R + r;
-                const bool real = i < k;
-                if (!real) i = k - 1;
-                const float t = static_cast<float>(i) * inv;
-                const WorkRef<STATS> w{&wk, real};
-                const bool c = pose_and_check<kStopAny, STATS, LMAX, SIMPLE>(
-                    P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, Ctl{kFull, false}, w);
-                if (__any_sync(kFull, c)) {
-                    collided = true;
-                    break;
-                }
-            }
-        }
-        if (lane == 0) valid[e] = collided ? 0 : 1;
-        if (STATS) {
-            wk.v[VP_WORK_EDGES_DONE] += (lane == 0);
-            flush_work<STATS>(wk, work, lane);
-        }
-        __syncwarp();
-    }
 }
 
 // One lane per configuration; lanes are independent (a warp stops once all
@@ -144,9 +19,9 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) states_kernel(const __grid_constan
                                                      const float *__restrict__ q, const long long N,
                                                      uint8_t *__restrict__ valid, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemCarve sc = carve(smem, env, P);
-    if (!stage_env(sc.env, env.data, env.n_float4, sc.bar, status)) return;
-    const EnvSm es = env_in_smem(sc.env, env);
+    const SmemCarve sc = env.staged ? carve<true>(smem, env, P) : carve<false>(smem, env, P);
+    if (!stage_env(sc.env, env, sc.bar, status)) return;
+    const EnvSm es = env_views_rt(sc.env, env);
     const Stash &stash = sc.stash;
     const int lane = threadIdx.x & 31;
     const int D = P.n_joints;
@@ -228,32 +103,15 @@ static cudaError_t prepare(K kernel, size_t smem, int block, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
 }
 
-// Instances: the counting variant always takes the general joint code.
-using PlainKernel = void (*)(const RobotParams, const EnvView, const float *, const float *, const int32_t *,
-                             const float, const long long, uint8_t *, unsigned *, unsigned long long *);
-template <int LMAX>
-static PlainKernel plain_instance(bool stats, bool simple) {
-    if (stats) return edges_plain_kernel<true, LMAX, false>;
-    return simple ? edges_plain_kernel<false, LMAX, true> : edges_plain_kernel<false, LMAX, false>;
-}
-
-static PlainKernel plain_kernel_for(int lmax, bool stats, bool simple) {
-    switch (lmax) {
-        case 8: return plain_instance<8>(stats, simple);
-        case 9: return plain_instance<9>(stats, simple);
-        case 15: return plain_instance<15>(stats, simple);
-        default: return plain_instance<17>(stats, simple);
-    }
-}
-
-cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, size_t smem, int block, int *blocks_per_sm) {
-    return prepare(plain_kernel_for(lmax, stats, simple), smem, block, blocks_per_sm);
+cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, bool staged, size_t smem, int block,
+                                int *blocks_per_sm) {
+    return prepare(kernel_set(lmax).plain[stats][simple][staged], smem, block, blocks_per_sm);
 }
 
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st) {
-    plain_kernel_for(lmax_for(P.n_links), work != nullptr, P.simple != 0)<<<grid, block, smem, st>>>(
+    kernel_set(lmax_for(P.n_links)).plain[work != nullptr][P.simple != 0][env.staged != 0]<<<grid, block, smem, st>>>(
         P, env, q0, q1, counts, res, E, valid, status, work);
     return cudaGetLastError();
 }

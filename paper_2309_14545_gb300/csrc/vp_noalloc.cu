@@ -157,7 +157,7 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int bps = 0;
-    e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, smem, block, &bps);
+    e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, ev.staged != 0, smem, block, &bps);
     // the array keeps the previous call's contents: restage the environment
     // and clear the status word on every call
     if (e == cudaSuccess && n4 > 0)

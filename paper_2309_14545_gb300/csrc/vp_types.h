@@ -90,7 +90,13 @@ struct EnvView {
     int ns, nc, nb;
     int n_float4;    // total float4 count
     int kind_order;  // visiting order of the kinds
+    int staged;      // 1: each block copies it into shared memory; 0: read in place (through L1)
 };
+
+// Dynamic shared memory the environment takes in a block.
+__host__ __device__ inline size_t env_smem_bytes(const EnvView &env) {
+    return env.staged ? static_cast<size_t>(env.n_float4) * 16 : 0;
+}
 
 // Primitive box margin: kBoxMarginAbs + kBoxMarginRel * (1 + max |coordinate|)
 // metres.  An fp32 ball test that reports contact implies a true distance

@@ -35,7 +35,8 @@ VP_WORK_N = 16
 EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load_env", "vp_fk_spheres",
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
-           "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling")
+           "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
+           "vp_screen_rounds")
 
 
 class VPError(RuntimeError):
@@ -80,6 +81,8 @@ def _load_lib():
         "vp_set_watchdog": (U, [P, C.c_double]),
         "vp_tiling": (U, [P, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_int)]),
         "vp_set_tiling": (U, [P, C.POINTER(C.c_int32), C.c_int]),
+        "vp_set_screen_rounds": (U, [P, C.c_int]),
+        "vp_screen_rounds": (U, [P, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +250,16 @@ def vp_set_tiling(ctx, lanes):
     lanes = [int(x) for x in lanes]
     arr = (C.c_int32 * max(1, len(lanes)))(*lanes)
     _check(ctx, lib.vp_set_tiling(ctx, arr, len(lanes)))
+
+
+def vp_set_screen_rounds(ctx, rounds):
+    _check(ctx, lib.vp_set_screen_rounds(ctx, int(rounds)))
+
+
+def vp_screen_rounds(ctx):
+    r = C.c_int(0)
+    _check(ctx, lib.vp_screen_rounds(ctx, C.byref(r)))
+    return r.value
 
 
 def vp_sync_status(ctx, stream=None):

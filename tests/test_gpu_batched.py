@@ -123,6 +123,31 @@ def test_batched_work_counters(vpmod):
         assert work[slot] % 32 == 0 and work[slot] >= live > 0
 
 
+@pytest.mark.parametrize("name,n", [(vpgen.TORSO8_OBB60_CAP20, 60_000), (vpgen.DUAL14_MIXED1000, 60_000),
+                                    (vpgen.ARM7_SPHERES16, 30_000)])
+def test_second_phase_matches_plain(vpmod, name, n):
+    """Edges handed to the second launch (after 1, 2 or 4 screening rounds,
+    or none) get the verdicts of the plain kernel, at several tilings."""
+    Validator, vp = vpmod
+    w = vpgen.workload(name, n_edges=n)
+    val = Validator(w.robot, w.env)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    want = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    assert 0 < want.mean() < 1
+    for rounds in (1, 2, 4, 0):
+        val.set_screen_rounds(rounds)
+        assert val.screen_rounds() == rounds
+        for lanes in ([4] * 9, [32] * 9, [4, 8, 16, 8, 4, 16, 8, 32, 16]):
+            val.set_tiling(lanes)
+            out = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+            val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
+            assert np.array_equal(out.cpu().numpy(), want), (rounds, lanes)
+    assert val.sync_status()[0] == vp.VP_OK
+    with pytest.raises(vp.VPError):
+        val.set_screen_rounds(-1)
+    val.close()
+
+
 def test_tiling_defaults_then_tuned(vpmod):
     Validator, vp = vpmod
     w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=100_000)
