@@ -203,6 +203,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain/batched/per-edge and grads legs")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--tiling", default=None,
+                    help="pin the batched tiling (9 comma-separated lanes per edge) instead of autotuning")
+    ap.add_argument("--screen", type=int, default=None, help="pin the screening rounds (with --tiling)")
     return ap.parse_args()
 
 
@@ -296,7 +299,11 @@ def run_native(args):
         k = counts if counts is not None else val.edge_counts(q0, q1, w.res, stream=stream)
         covered = float(k.to(torch.int64).clamp(min=0).sum().item())
         if mode == vp.VP_MODE_BATCHED:
-            val.autotune(q0, q1, counts, w.res, stream=stream)
+            if args.tiling:
+                val.set_tiling([int(x) for x in args.tiling.split(",")])
+                val.set_screen_rounds(args.screen if args.screen is not None else 0)
+            else:
+                val.autotune(q0, q1, counts, w.res, stream=stream)
         # work counters (untimed): the FLOP numerator of the roofline
         _, work = val.validate_edges_work(q0, q1, counts, w.res, mode=mode, stream=stream)
         work = work.cpu().numpy()
@@ -401,6 +408,9 @@ def run_native(args):
                   "covered_states_per_step": covered_all, "valid_edge_fraction": valid_frac,
                   "work_per_step": {n: int(work[i]) for i, n in enumerate(WORK_NAMES)},
                   "lane_efficiency": lane_efficiency(work),
+                  "tiling": val.tiling() if mode == vp.VP_MODE_BATCHED else None,
+                  "screen_rounds": val.screen_rounds() if mode == vp.VP_MODE_BATCHED else None,
+                  "tiling_source": ("pinned" if args.tiling else "autotuned") if mode == vp.VP_MODE_BATCHED else None,
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
     if not args.no_compare:

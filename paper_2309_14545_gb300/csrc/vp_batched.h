@@ -20,7 +20,7 @@ constexpr int kCtrlSurv = 33;    // ctrl[33]     edges left to the second phase
 constexpr int kCtrlQueue2 = 34;  // ctrl[34]     second-phase work-item counter
 constexpr int kCtrlInts = 64;
 constexpr int kSplit = 16;       // second-phase work items per edge
-constexpr int kDefaultScreenRounds = 4;
+constexpr int kDefaultScreenRounds = 0;
 
 struct BatchPlan {
     int G[kNB];            // lanes per edge, per bucket

@@ -284,6 +284,35 @@ __device__ __forceinline__ void recompute_frame_cached(const RobotParams &P, int
     }
 }
 
+// A link frame kept between requests: the frame of the last link asked for,
+// and the joints on its path.  A request for a descendant link (whose path
+// contains the kept one) only applies the joints past it -- joints are
+// numbered parents first, so those come after every kept joint -- and any
+// other request starts again from the base.  Fine tests and self-pair groups
+// visit links in ascending order, so most requests extend the kept frame.
+struct FrameCursor {
+    Fr f;
+    unsigned done = ~0u;  // path mask of f (~0: nothing kept)
+};
+
+template <bool SIMPLE>
+__device__ __forceinline__ const Fr &frame_at(const RobotParams &P, int l, const Stash &st, FrameCursor &c) {
+    const unsigned path = P.links[l].path;
+    unsigned m = path & ~c.done;
+    if ((path & c.done) != c.done) {
+        fr_identity(c.f);
+        m = path;
+    }
+#pragma unroll 1
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        apply_joint_sc<SIMPLE>(P.joints[j], st.mo(j, 0), st.mo(j, 1), c.f);
+    }
+    c.done = path;
+    return c.f;
+}
+
 // ---------------------------------------------------------------------------
 // work counters (only in the counting variant)
 
@@ -444,8 +473,8 @@ __device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const S
 // Returns the warp's stop decision.
 template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE>
 __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, const float4 *boxes, int n,
-                                          const LinkBox &lb, const Stash &stash, Ctl &ctl, bool &col,
-                                          const WorkRef<STATS> &w) {
+                                          const LinkBox &lb, const Stash &stash, FrameCursor &fc, Ctl &ctl,
+                                          bool &col, const WorkRef<STATS> &w) {
     using K = Kind<KIND>;
     constexpr int PB = 32 / LMAX > 0 ? 32 / LMAX : 1;  // primitives per batch
     constexpr unsigned kLinks = (1u << LMAX) - 1u;
@@ -485,8 +514,7 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                 const int l = __ffs(any) - 1;
                 any &= any - 1;
                 const LinkC &L = P.links[l];
-                Fr f;
-                recompute_frame_cached<SIMPLE>(P, l, stash, f);
+                const Fr &f = frame_at<SIMPLE>(P, l, stash, fc);
                 w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
                 if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
                 const bool h = (bits >> l) & 1u;
@@ -550,11 +578,10 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             }
         }
     }
-    // 2. self pairs (groups sorted by later link: its frame is reused
-    //    across consecutive groups; the earlier link's too while it repeats)
+    // 2. self pairs (groups sorted by later link, then earlier link: each
+    //    side's frame cursor mostly extends the frame it already holds)
     {
-        Fr fa, fb;
-        int la_cached = -1, lb_cached = -1;
+        FrameCursor cur_a, cur_b;
         for (int g = 0; g < P.n_groups; ++g) {
             const GroupC G = P.groups[g];
             const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
@@ -563,14 +590,8 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
             if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
             if (__any_sync(kFull, wants(ctl, h))) {
-                if (G.lb != lb_cached) {
-                    recompute_frame_cached<SIMPLE>(P, G.lb, stash, fb);
-                    lb_cached = G.lb;
-                }
-                if (G.la != la_cached) {
-                    recompute_frame_cached<SIMPLE>(P, G.la, stash, fa);
-                    la_cached = G.la;
-                }
+                const Fr &fb = frame_at<SIMPLE>(P, G.lb, stash, cur_b);
+                const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
                 w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
                 if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
 #pragma unroll 1
@@ -589,15 +610,16 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
     }
     // 3. primitives against every link, culled by warp-wide link boxes
     const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
+    FrameCursor fc;
     for (int ki = 0; ki < 3; ++ki) {
         const int kind = (env.kind_order >> (4 * ki)) & 15;
         bool stop;
         if (kind == 0)
-            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, ctl, col, w);
+            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl, col, w);
         else if (kind == 1)
-            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, ctl, col, w);
+            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl, col, w);
         else
-            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, ctl, col, w);
+            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl, col, w);
         if (stop) return col;
     }
     return col;
