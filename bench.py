@@ -46,7 +46,7 @@ FLOPS_PAIR_COARSE = 10            # link centres already posed
 FLOPS_PAIR_FINE = 2 * FLOPS_CENTRE + 10
 WORK_NAMES = ("states", "link_centres", "coarse_sphere", "coarse_capsule", "coarse_cuboid", "fine_sphere",
               "fine_capsule", "fine_cuboid", "pair_coarse", "pair_fine", "edges", "lane_states", "lane_coarse",
-              "lane_fine", "lane_pair_fine", "box_tests")
+              "lane_fine", "lane_pair_fine", "box_tests", "fine_own", "pair_fine_own")
 
 
 def _git_rev():

@@ -203,7 +203,11 @@ enum {
     VP_WORK_LANE_PAIR_FINE, /* sphere-pair tests                              */
     VP_WORK_BOX_TESTS,      /* (link, primitive) world-box overlap tests that
                              * cull coarse tests (one per pair per warp)      */
-    VP_WORK_N = 16
+    VP_WORK_FINE_OWN,       /* fine primitive tests on lanes whose own coarse
+                             * test hit the link (the rest run in lockstep)   */
+    VP_WORK_PAIR_FINE_OWN,  /* sphere-pair tests on lanes whose own link-pair
+                             * test hit                                       */
+    VP_WORK_N = 32
 };
 vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                                  float resolution, int64_t n_edges, uint8_t *valid, int mode, uint64_t *work,

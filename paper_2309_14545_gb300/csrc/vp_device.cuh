@@ -518,6 +518,7 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                 w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
                 if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
                 const bool h = (bits >> l) & 1u;
+                if (h) w.add(VP_WORK_FINE_OWN, L.s1 - L.s0);
 #pragma unroll 1
                 for (int s = L.s0; s < L.s1; ++s) {
                     const float4 sp = P.spheres[s];
@@ -594,6 +595,7 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
                 const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
                 w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
                 if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+                if (!ctl.idle && h) w.add(VP_WORK_PAIR_FINE_OWN, G.p1 - G.p0);
 #pragma unroll 1
                 for (int p = G.p0; p < G.p1; ++p) {
                     const PairC pr = P.pairs[p];

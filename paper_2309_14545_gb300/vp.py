@@ -28,8 +28,8 @@ VP_MAX_STEPS = 16777216
 (VP_WORK_STATES, VP_WORK_LINK_CENTRES, VP_WORK_COARSE_SPHERE, VP_WORK_COARSE_CAPSULE, VP_WORK_COARSE_CUBOID,
  VP_WORK_FINE_SPHERE, VP_WORK_FINE_CAPSULE, VP_WORK_FINE_CUBOID, VP_WORK_PAIR_COARSE, VP_WORK_PAIR_FINE,
  VP_WORK_EDGES_DONE, VP_WORK_LANE_STATES, VP_WORK_LANE_COARSE, VP_WORK_LANE_FINE,
- VP_WORK_LANE_PAIR_FINE, VP_WORK_BOX_TESTS) = range(16)
-VP_WORK_N = 16
+ VP_WORK_LANE_PAIR_FINE, VP_WORK_BOX_TESTS, VP_WORK_FINE_OWN, VP_WORK_PAIR_FINE_OWN) = range(18)
+VP_WORK_N = 32
 
 #: Every symbol include/vp.h declares.
 EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load_env", "vp_fk_spheres",

@@ -121,6 +121,9 @@ def test_batched_work_counters(vpmod):
     for slot, live in ((vp.VP_WORK_LANE_STATES, work[vp.VP_WORK_STATES]), (vp.VP_WORK_LANE_COARSE, coarse),
                        (vp.VP_WORK_LANE_FINE, fine), (vp.VP_WORK_LANE_PAIR_FINE, work[vp.VP_WORK_PAIR_FINE])):
         assert work[slot] % 32 == 0 and work[slot] >= live > 0
+    # lanes whose own coarse test hit are a subset of the live lanes
+    assert 0 < work[vp.VP_WORK_FINE_OWN] <= fine
+    assert 0 < work[vp.VP_WORK_PAIR_FINE_OWN] <= work[vp.VP_WORK_PAIR_FINE]
 
 
 @pytest.mark.parametrize("name,n", [(vpgen.TORSO8_OBB60_CAP20, 60_000), (vpgen.DUAL14_MIXED1000, 60_000),
