@@ -410,6 +410,7 @@ def run_native(args):
                   "lane_efficiency": lane_efficiency(work),
                   "tiling": val.tiling() if mode == vp.VP_MODE_BATCHED else None,
                   "screen_rounds": val.screen_rounds() if mode == vp.VP_MODE_BATCHED else None,
+                  "prims_first": val.check_order(),
                   "tiling_source": ("pinned" if args.tiling else "autotuned") if mode == vp.VP_MODE_BATCHED else None,
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }

@@ -266,6 +266,15 @@ vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n);
 vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds);
 vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 
+/* Check order of the validation kernels (edges and states, every mode):
+ * after posing, self pairs then primitives (prims_first = 0, the default),
+ * or primitives then self pairs (1).  Which finds a colliding configuration
+ * with less work depends on the robot and scene; vp_autotune times both.
+ * vp_set_check_order pins it (VP_ERR_ARG unless 0 or 1) until the next
+ * vp_autotune or load.  The verdicts do not depend on it. */
+vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
+vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
+
 /* Synchronise `stream`, read and clear the device status word: VP_OK,
  * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are
  * returned in *bits when bits != NULL. */

@@ -88,6 +88,13 @@ class Validator:
     def set_screen_rounds(self, rounds):
         vp.vp_set_screen_rounds(self.ctx, rounds)
 
+    def check_order(self):
+        """1 if primitives are checked before self pairs, else 0."""
+        return vp.vp_check_order(self.ctx)
+
+    def set_check_order(self, prims_first):
+        vp.vp_set_check_order(self.ctx, prims_first)
+
     def collision_cost(self, q, margin, grad=False, stream=None):
         cost = torch.empty(q.shape[0], dtype=torch.float32, device=self._dev())
         g = torch.empty_like(q) if grad else None

@@ -439,6 +439,7 @@ extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, 
             ctx, [lmax](size_t sm, int b, bool, int *o) { return prepare_states(lmax, sm, b, o); }, &view, &block, &smem,
             &bps, &e))
         return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
+    view.prims_first = batched_check_order(ctx->batched);
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
         const int64_t grid =
@@ -507,6 +508,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
         return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges (prepare)");
     if (bps < 1) return fail(ctx, VP_ERR_CAPACITY, "plain edge kernel cannot be resident");
+    view.prims_first = batched_check_order(ctx->batched);
     const int wpb = block / 32;
     if (mode == VP_MODE_PER_EDGE && !work) {
         const int D = ctx->robot.n_joints;
@@ -633,6 +635,19 @@ extern "C" vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds) {
 extern "C" vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds) {
     if (!ctx || !rounds) return VP_ERR_ARG;
     *rounds = batched_screen_rounds(ctx->batched);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int prims_first) {
+    if (!ctx) return VP_ERR_ARG;
+    if (prims_first != 0 && prims_first != 1) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 or 1");
+    batched_set_check_order(ctx->batched, prims_first);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_check_order(vp_ctx *ctx, int *prims_first) {
+    if (!ctx || !prims_first) return VP_ERR_ARG;
+    *prims_first = batched_check_order(ctx->batched);
     return VP_OK;
 }
 

@@ -134,6 +134,7 @@ struct Impl {
     float k_res = 0.f;
     int G[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     int screen_rounds = kDefaultScreenRounds;
+    int prims_first = 0;  // check order
     bool tuned = false;
 };
 
@@ -278,6 +279,7 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     EnvView view;
     rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
+    view.prims_first = im->prims_first;
     const bool same = im->exec && im->k_q0 == a.q0 && im->k_q1 == a.q1 && im->k_counts == a.counts &&
                       im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res && im->k_ev == a.ev_start &&
                       im->k_watchdog == st.watchdog_ns;
@@ -321,6 +323,7 @@ int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *wor
     EnvView view;
     rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
+    view.prims_first = im->prims_first;
     const cudaError_t e = enqueue(im, a, view, plan_from(im, st.watchdog_ns), smem, grid, a.stream, a.valid, work);
     return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
 }
@@ -342,6 +345,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     EnvView view;
     int rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
+    view.prims_first = im->prims_first;
     const int64_t S = std::min<int64_t>(a.E, int64_t{1} << 23);
     rc = ensure_capacity(im, S, msg);
     if (rc) return rc;
@@ -379,6 +383,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         if (it != g_tune_cache.end()) {
             for (int b = 0; b < kNB; ++b) im->G[b] = it->second[b];
             im->screen_rounds = it->second[kNB];
+            im->prims_first = it->second[kNB + 1];
             im->tuned = true;
             drop_graph(im);
             cudaFree(tv);
@@ -400,6 +405,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) p.G[b] = defaults[b];
     p.screen_rounds = kDefaultScreenRounds;
+    view.prims_first = 0;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -451,6 +457,18 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         p.screen_rounds = best_r;
         cur = best;
     };
+    // check order (self pairs or primitives first), the other choices held
+    auto tune_order = [&]() {
+        const int keep = view.prims_first;
+        view.prims_first = 1 - keep;
+        float ms = 0.f;
+        time_plan(&ms);
+        if (e == cudaSuccess && ms < 0.99f * cur)
+            cur = ms;
+        else
+            view.prims_first = keep;
+    };
+    tune_order();
     tune_screen();
     const int options[4] = {4, 8, 16, 32};
     bool moved = true;
@@ -478,18 +496,21 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         }
     }
     if (e == cudaSuccess) tune_screen();
+    if (e == cudaSuccess) tune_order();
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(tv);
     if (e != cudaSuccess) return set_err(msg, "tuning runs", e);
     for (int b = 0; b < kNB; ++b) im->G[b] = p.G[b];
     im->screen_rounds = p.screen_rounds;
+    im->prims_first = view.prims_first;
     im->tuned = true;
     drop_graph(im);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         std::vector<int> v(im->G, im->G + kNB);
         v.push_back(im->screen_rounds);
+        v.push_back(im->prims_first);
         g_tune_cache[key] = v;
     }
     return 0;
@@ -503,6 +524,7 @@ void batched_invalidate(BatchedState &st) {
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) im->G[b] = defaults[b];
     im->screen_rounds = kDefaultScreenRounds;
+    im->prims_first = 0;
 }
 
 void batched_release(BatchedState &st) {
@@ -528,6 +550,18 @@ void batched_set_screen_rounds(BatchedState &st, int rounds) {
 int batched_screen_rounds(const BatchedState &st) {
     const Impl *im = static_cast<const Impl *>(st.impl);
     return im ? im->screen_rounds : kDefaultScreenRounds;
+}
+
+void batched_set_check_order(BatchedState &st, int prims_first) {
+    Impl *im = impl_of(st);
+    im->prims_first = prims_first;
+    im->tuned = true;
+    drop_graph(im);
+}
+
+int batched_check_order(const BatchedState &st) {
+    const Impl *im = static_cast<const Impl *>(st.impl);
+    return im ? im->prims_first : 0;
 }
 
 void batched_set_tiling(BatchedState &st, const int *G, int n) {

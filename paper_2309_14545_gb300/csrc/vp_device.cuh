@@ -343,6 +343,7 @@ struct EnvSm {
     const float4 *bb_sph, *bb_cap, *bb_box;  // world boxes [2 n] of each kind
     int ns, nc, nb;
     int kind_order;     // kinds in visiting order, 4 bits each
+    int prims_first;    // 1: primitives before self pairs
 };
 
 // Views of the environment: the block's shared copy (STAGED), or the device
@@ -361,6 +362,7 @@ __device__ __forceinline__ EnvSm env_views(const float4 *sm, const EnvView &env)
     e.nc = env.nc;
     e.nb = env.nb;
     e.kind_order = env.kind_order;
+    e.prims_first = env.prims_first;
     return e;
 }
 
@@ -540,6 +542,7 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 //   3. primitives, kind by kind, each against every link's bounding sphere
 //      (pairs first culled by warp-wide boxes, see prim_pass), then fine
 //      spheres where a coarse test hit.
+// Steps 2 and 3 swap when the environment view says so (prims_first).
 // Frames needed by fine tests are recomputed from the kept (sin, cos).  The
 // order of checks is chosen for early exit: a colliding configuration is
 // most often found by a self pair or a large primitive; it does not change
@@ -579,50 +582,61 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
             }
         }
     }
-    // 2. self pairs (groups sorted by later link, then earlier link: each
-    //    side's frame cursor mostly extends the frame it already holds)
-    {
-        FrameCursor cur_a, cur_b;
-        for (int g = 0; g < P.n_groups; ++g) {
-            const GroupC G = P.groups[g];
-            const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
-            const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
-            const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
-            const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
-            if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
-            if (__any_sync(kFull, wants(ctl, h))) {
-                const Fr &fb = frame_at<SIMPLE>(P, G.lb, stash, cur_b);
-                const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
-                w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
-                if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
-                if (!ctl.idle && h) w.add(VP_WORK_PAIR_FINE_OWN, G.p1 - G.p0);
+    // 2./3. self pairs, and primitives against every link, in the order the
+    //    environment view gives (which finds a colliding state sooner
+    //    depends on the scene: self contact for two arms in free space,
+    //    obstacles for one arm in clutter).  Self-pair groups are sorted by
+    //    later link, then earlier link, so each side's frame cursor mostly
+    //    extends the frame it holds; primitive pairs are culled by warp-wide
+    //    link boxes.
 #pragma unroll 1
-                for (int p = G.p0; p < G.p1; ++p) {
-                    const PairC pr = P.pairs[p];
-                    const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
-                    const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
-                    const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
-                    const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
-                    const float r2 = sa.w + sb.w;
-                    col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+    for (int phase = 0; phase < 2; ++phase) {
+        if ((phase == 0) != (env.prims_first != 0)) {  // self pairs
+            FrameCursor cur_a, cur_b;
+            for (int g = 0; g < P.n_groups; ++g) {
+                const GroupC G = P.groups[g];
+                const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
+                const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+                const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
+                const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+                if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
+                if (__any_sync(kFull, wants(ctl, h))) {
+                    const Fr &fb = frame_at<SIMPLE>(P, G.lb, stash, cur_b);
+                    const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
+                    w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
+                    if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+                    if (!ctl.idle && h) w.add(VP_WORK_PAIR_FINE_OWN, G.p1 - G.p0);
+#pragma unroll 1
+                    for (int p = G.p0; p < G.p1; ++p) {
+                        const PairC pr = P.pairs[p];
+                        const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
+                        const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
+                        const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
+                        const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+                        const float r2 = sa.w + sb.w;
+                        col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+                    }
+                    if (group_stop<MODE>(ctl, col)) return col;
                 }
-                if (group_stop<MODE>(ctl, col)) return col;
+            }
+        } else {  // primitives
+            const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
+            FrameCursor fc;
+            for (int ki = 0; ki < 3; ++ki) {
+                const int kind = (env.kind_order >> (4 * ki)) & 15;
+                bool stop;
+                if (kind == 0)
+                    stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl,
+                                                                col, w);
+                else if (kind == 1)
+                    stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl,
+                                                                col, w);
+                else
+                    stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl,
+                                                                col, w);
+                if (stop) return col;
             }
         }
-    }
-    // 3. primitives against every link, culled by warp-wide link boxes
-    const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
-    FrameCursor fc;
-    for (int ki = 0; ki < 3; ++ki) {
-        const int kind = (env.kind_order >> (4 * ki)) & 15;
-        bool stop;
-        if (kind == 0)
-            stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl, col, w);
-        else if (kind == 1)
-            stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl, col, w);
-        else
-            stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl, col, w);
-        if (stop) return col;
     }
     return col;
 }

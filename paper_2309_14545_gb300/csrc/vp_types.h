@@ -91,6 +91,7 @@ struct EnvView {
     int n_float4;    // total float4 count
     int kind_order;  // visiting order of the kinds
     int staged;      // 1: each block copies it into shared memory; 0: read in place (through L1)
+    int prims_first; // check order: 1 = primitives before self pairs (set per launch)
 };
 
 // Dynamic shared memory the environment takes in a block.

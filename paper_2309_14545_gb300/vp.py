@@ -36,7 +36,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
-           "vp_screen_rounds")
+           "vp_screen_rounds", "vp_set_check_order", "vp_check_order")
 
 
 class VPError(RuntimeError):
@@ -83,6 +83,8 @@ def _load_lib():
         "vp_set_tiling": (U, [P, C.POINTER(C.c_int32), C.c_int]),
         "vp_set_screen_rounds": (U, [P, C.c_int]),
         "vp_screen_rounds": (U, [P, C.POINTER(C.c_int)]),
+        "vp_set_check_order": (U, [P, C.c_int]),
+        "vp_check_order": (U, [P, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -259,6 +261,16 @@ def vp_set_screen_rounds(ctx, rounds):
 def vp_screen_rounds(ctx):
     r = C.c_int(0)
     _check(ctx, lib.vp_screen_rounds(ctx, C.byref(r)))
+    return r.value
+
+
+def vp_set_check_order(ctx, prims_first):
+    _check(ctx, lib.vp_set_check_order(ctx, int(prims_first)))
+
+
+def vp_check_order(ctx):
+    r = C.c_int(0)
+    _check(ctx, lib.vp_check_order(ctx, C.byref(r)))
     return r.value
 
 

@@ -145,9 +145,21 @@ def test_second_phase_matches_plain(vpmod, name, n):
             out = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
             val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
             assert np.array_equal(out.cpu().numpy(), want), (rounds, lanes)
+    # the other check order: the same verdicts in both modes, and for states
+    states = q0[: min(n, 20000)]
+    want_s = val.validate_states(states).cpu().numpy()
+    val.set_check_order(1)
+    assert val.check_order() == 1
+    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
+        got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
+        assert np.array_equal(got, want), mode
+    assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s)
+    val.set_check_order(0)
     assert val.sync_status()[0] == vp.VP_OK
     with pytest.raises(vp.VPError):
         val.set_screen_rounds(-1)
+    with pytest.raises(vp.VPError):
+        val.set_check_order(2)
     val.close()
 
 
