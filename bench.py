@@ -206,6 +206,8 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="pin the batched tiling (9 comma-separated lanes per edge) instead of autotuning")
     ap.add_argument("--screen", type=int, default=None, help="pin the screening rounds (with --tiling)")
+    ap.add_argument("--check-order", type=int, default=None, choices=[0, 1],
+                    help="pin the check order (1: primitives before self pairs); with --tiling, or in plain mode")
     return ap.parse_args()
 
 
@@ -302,8 +304,11 @@ def run_native(args):
             if args.tiling:
                 val.set_tiling([int(x) for x in args.tiling.split(",")])
                 val.set_screen_rounds(args.screen if args.screen is not None else 0)
+                val.set_check_order(args.check_order or 0)
             else:
                 val.autotune(q0, q1, counts, w.res, stream=stream)
+        elif args.check_order is not None:
+            val.set_check_order(args.check_order)
         # work counters (untimed): the FLOP numerator of the roofline
         _, work = val.validate_edges_work(q0, q1, counts, w.res, mode=mode, stream=stream)
         work = work.cpu().numpy()
@@ -522,7 +527,7 @@ def _traffic(args, E, mode):
     try:
         rec = json.load(open(path))
         from paper_2309_14545_gb300 import build
-        if rec.get("sources_hash") != build.sources_hash():
+        if rec.get("kernel_hash") != build.kernel_hash():
             return None
         ent = rec.get(f"{args.workload}-{'batched' if mode == 1 else 'plain'}")
         if not ent:

@@ -29,11 +29,19 @@ def _deps():
     return glob.glob(os.path.join(CSRC, "*")) + [os.path.join(HERE, "..", "include", "vp.h")]
 
 
-def sources_hash() -> str:
-    """Hash of the kernel sources and the public header (identifies a build)."""
+# The files that define the edge-validation kernels (device code, tables and
+# their layouts); host-side launch code, the tuner and other kernels are not.
+KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_inst_l8.cu", "vp_inst_l9.cu",
+                "vp_inst_l15.cu", "vp_inst_l17.cu")
+
+
+def kernel_hash() -> str:
+    """Hash of the edge-validation kernels' sources and the public header:
+    counters measured on one build (profiles/traffic.json) apply to another
+    with the same hash."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*"))) + [os.path.join(HERE, "..", "include", "vp.h")]:
+    for p in [os.path.join(CSRC, f) for f in KERNEL_FILES] + [os.path.join(HERE, "..", "include", "vp.h")]:
         h.update(os.path.basename(p).encode())
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]

@@ -110,12 +110,13 @@ __device__ __forceinline__ float ball_cost(float3 x, float r, const EnvSm &env, 
     return c;
 }
 
+template <bool STAGED>
 __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                    const float *__restrict__ q, const long long N, const float margin,
                                                    float *__restrict__ cost, float *__restrict__ grad,
                                                    unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    size_t off = env_smem_bytes(env);
+    size_t off = STAGED ? static_cast<size_t>(env_prim_float4(env)) * 16 : 0;  // no boxes: the cost has no cull
     float4 *env_sm = reinterpret_cast<float4 *>(smem);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
     off += 16;
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
     stash.centres = nullptr;
     stash.motion = nullptr;
     stash.stride = static_cast<int>(blockDim.x);
-    if (!stage_env(env_sm, env, bar, status)) return;
-    const EnvSm es = env_views_rt(env_sm, env);
+    if (STAGED && !stage_env(env_sm, env, bar, status, env_prim_float4(env))) return;
+    const EnvSm es = env_views<STAGED>(env_sm, env);
     const int D = P.n_joints;
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -229,14 +230,18 @@ int cost_launch(const RobotParams &P, const EnvView &env, const float *q, int64_
                                      sizeof(float);
         EnvView vst = env;
         vst.staged = 1;
-        const size_t m_st = env_smem_bytes(vst) + rest;
+        const size_t m_st = static_cast<size_t>(env_prim_float4(vst)) * 16 + rest;
         if (rest > smem_optin) continue;
         const size_t m_max = m_st <= smem_optin ? m_st : rest;
-        e = cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m_max));
+        e = cudaFuncSetAttribute(cost_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(m_max));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cost_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(rest));
         int b_in = 0, b_st = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_in, cost_kernel, b, rest);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_in, cost_kernel<false>, b, rest);
         if (e == cudaSuccess && m_st <= smem_optin)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_st, cost_kernel, b, m_st);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_st, cost_kernel<true>, b, m_st);
         if (e != cudaSuccess) break;
         view.staged = (b_st >= 1 && b_st >= b_in) ? 1 : 0;
         smem = view.staged ? m_st : rest;
@@ -251,7 +256,8 @@ int cost_launch(const RobotParams &P, const EnvView &env, const float *q, int64_
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(std::max(bps, 1)) * num_sms));
-        cost_kernel<<<static_cast<unsigned>(grid), block, smem, st>>>(P, view, q, n, margin, cost, grad, status);
+        (view.staged ? cost_kernel<true> : cost_kernel<false>)<<<static_cast<unsigned>(grid), block, smem, st>>>(
+            P, view, q, n, margin, cost, grad, status);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

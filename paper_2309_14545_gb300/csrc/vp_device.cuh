@@ -182,10 +182,13 @@ __device__ __forceinline__ uint64_t global_ns() {
 // cp.async.bulk completing on an mbarrier.  Every thread of the block calls
 // this.  The wait is bounded (about one second); on expiry the status word
 // gets VP_DEVERR_TIMEOUT and false is returned (the block must not use dst).
-__device__ __forceinline__ bool stage_env(float4 *dst, const EnvView &env, uint64_t *bar, unsigned *status) {
-    if (!env.staged || env.n_float4 == 0) return true;  // read in place
+// n_float4: how much of the buffer to copy (default all of it).
+__device__ __forceinline__ bool stage_env(float4 *dst, const EnvView &env, uint64_t *bar, unsigned *status,
+                                          int n_float4 = -1) {
+    if (n_float4 < 0) n_float4 = env.n_float4;
+    if (!env.staged || n_float4 == 0) return true;  // read in place
     const float4 *src = env.data;
-    const uint32_t bytes = static_cast<uint32_t>(env.n_float4) * 16u;
+    const uint32_t bytes = static_cast<uint32_t>(n_float4) * 16u;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

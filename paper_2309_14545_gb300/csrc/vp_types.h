@@ -99,6 +99,9 @@ __host__ __device__ inline size_t env_smem_bytes(const EnvView &env) {
     return env.staged ? static_cast<size_t>(env.n_float4) * 16 : 0;
 }
 
+// float4s of the primitive data alone (the boxes that follow are for culling).
+__host__ __device__ inline int env_prim_float4(const EnvView &env) { return env.ns + 2 * env.nc + 4 * env.nb; }
+
 // Primitive box margin: kBoxMarginAbs + kBoxMarginRel * (1 + max |coordinate|)
 // metres.  An fp32 ball test that reports contact implies a true distance
 // below the radius plus a few ulp of the coordinates (about 1e-6 m per metre
