@@ -393,6 +393,10 @@ def run_native(args):
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = 2 * 128 * n_sm * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
     achieved = flops / (kms / 1000.0) / 1e12
+    try:  # the device's own FMA rate (independent chains, all SMs), untimed
+        peak_measured = vp.vp_measure_fp32_peak(local, 1.0)
+    except Exception:
+        peak_measured = None
     valid_frac = float(valid.float().mean().item())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -403,10 +407,13 @@ def run_native(args):
                      "kernel_ms": kms,
                      "peak_basis": f"FP32 FMA: 128 lanes x 2 flops x {n_sm} SMs x {sm_max:.0f} MHz (derived)",
                      "kernel": "edges_plain_kernel" if mode == vp.VP_MODE_PLAIN else "edges_batched_kernel",
-                     "flops_per_step": flops},
+                     "flops_per_step": flops,
+                     "peak_measured": peak_measured,
+                     "frac_of_measured": achieved / peak_measured if peak_measured else None,
+                     "peak_measured_basis": "vp_measure_fp32_peak: independent FFMA chains on every SM"},
         "e2e": {"value": covered_all / (e2e_step / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
-        "gpu_launches": args.steps * (3 if mode == vp.VP_MODE_BATCHED else 1),
+        "gpu_launches": args.steps * (4 if mode == vp.VP_MODE_BATCHED else 1),
         "clocks": clocks,
         "extra": {"mode": args.mode, "edges_per_s": edges_all / (t_max / 1000.0),
                   "evaluated_states_per_s": world * int(work[vp.VP_WORK_STATES]) / (t_max / 1000.0),
@@ -424,7 +431,9 @@ def run_native(args):
         line["grads"] = grads_leg(dev, flush, stream)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                                "one_thread": {"value": r1, "sample": sample1}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -451,7 +460,8 @@ def _timed(fn, flush, stream, reps):
 def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
     """Plain single launch vs batched on the headline workload, and on the
     dual-arm workloads (shelves: also one plain launch per edge; 1,000
-    primitives: 4,194,304 edges).  Verdicts must be identical across modes."""
+    primitives: 4,194,304 edges) and their obstacle-shifted variants.
+    Verdicts must be identical across modes."""
     import torch
     from paper_2309_14545_gb300 import Validator, vp
     res = {}
@@ -483,7 +493,8 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
         return d
 
     res[w.name] = leg(val, q0, q1, counts, float(w.res), q0.shape[0], 3)
-    for name, per_edge in ((vpgen.DUAL14_SHELVES, True), (vpgen.DUAL14_MIXED1000, False)):
+    for name, per_edge in ((vpgen.DUAL14_SHELVES, True), (vpgen.DUAL14_MIXED1000, False),
+                           (vpgen.DUAL14_SHELVES_FAR, False), (vpgen.DUAL14_MIXED1000_FAR, False)):
         wc = vpgen.workload(name)
         vc = Validator(wc.robot, wc.env, device=dev.index)
         with torch.cuda.stream(stream):

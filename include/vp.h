@@ -275,6 +275,15 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
 vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
 
+/* Measured FP32 FMA throughput of CUDA device `device` in TFLOP/s (an FMA is
+ * two flops): independent FMA chains on every SM at full occupancy, one
+ * launch grown to about seconds / 4, best of three (0 < seconds <= 60; the
+ * call takes about that long).  A measurement hook: the denominator the
+ * validation kernels' FLOP rate is reported against beside the one derived
+ * from lane counts and the clock.  Synchronous; the current device is left
+ * unchanged. */
+vp_status vp_measure_fp32_peak(int device, double seconds, double *tflops);
+
 /* Synchronise `stream`, read and clear the device status word: VP_OK,
  * VP_ERR_DEVICE (count / length bits) or VP_ERR_TIMEOUT.  The bits are
  * returned in *bits when bits != NULL. */

@@ -25,6 +25,7 @@ struct vp_ctx {
     std::vector<uint16_t> sorted_of;  // caller's sphere index -> sorted index
     float4 *env_buf = nullptr;
     EnvView env{};
+    uint64_t env_hash = 0;       // contents of the packed environment (tuning-cache key)
     bool env_loaded = false;
     unsigned *status = nullptr;  // device status word
     BatchedState batched;        // scratch and tuned tiling of the batched mode
@@ -360,6 +361,12 @@ extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
     ctx->env_buf = buf;
     view.data = buf;
     ctx->env = view;
+    {  // FNV-1a over the packed bytes
+        uint64_t hsh = 1469598103934665603ull;
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(h.data());
+        for (size_t i = 0; i < n4 * 16; ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+        ctx->env_hash = hsh;
+    }
     ctx->env_loaded = true;
     batched_invalidate(ctx->batched);
     return VP_OK;
@@ -483,6 +490,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     if (mode == VP_MODE_BATCHED) {
         BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, valid, ctx->status,
                       ctx->num_sms, ctx->smem_optin, st};
+        a.env_hash = ctx->env_hash;
         if (timed) {
             a.ev_start = ctx->ev_start;
             a.ev_stop = ctx->ev_stop;
@@ -568,6 +576,7 @@ extern "C" vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, 
     DeviceGuard g(ctx->device);
     BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, nullptr, ctx->status,
                   ctx->num_sms, ctx->smem_optin, static_cast<cudaStream_t>(stream)};
+    a.env_hash = ctx->env_hash;
     std::string msg;
     const int rc = batched_autotune(ctx->batched, a, &msg);
     if (rc == 0) return VP_OK;

@@ -109,9 +109,11 @@ size_t batched_smem(const EnvView &env, const RobotParams &P) {
 struct TuneKey {
     std::vector<unsigned char> robot;
     int ns, nc, nb, sms;
+    uint64_t env;              // contents of the environment: placement changes the best choice
     std::vector<int> profile;  // length histogram, coarse
     bool operator<(const TuneKey &o) const {
-        return std::tie(robot, ns, nc, nb, sms, profile) < std::tie(o.robot, o.ns, o.nc, o.nb, o.sms, o.profile);
+        return std::tie(robot, ns, nc, nb, sms, env, profile) <
+               std::tie(o.robot, o.ns, o.nc, o.nb, o.sms, o.env, o.profile);
     }
 };
 
@@ -375,6 +377,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     key.nc = a.env->nc;
     key.nb = a.env->nb;
     key.sms = a.num_sms;
+    key.env = a.env_hash;
     for (int b = 0; b < kNB; ++b)
         key.profile.push_back(hist[b] == 0 ? 0 : 1 + static_cast<int>((20 * static_cast<int64_t>(hist[b])) / S));
     {

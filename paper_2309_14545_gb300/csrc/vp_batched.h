@@ -69,6 +69,7 @@ struct BatchedArgs {
     size_t smem_optin;
     cudaStream_t stream;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // timing events around the persistent kernel
+    uint64_t env_hash = 0;  // contents of the packed environment (tuning-cache key)
 };
 
 struct BatchedState {

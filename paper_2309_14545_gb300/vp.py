@@ -36,7 +36,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
-           "vp_screen_rounds", "vp_set_check_order", "vp_check_order")
+           "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak")
 
 
 class VPError(RuntimeError):
@@ -85,6 +85,7 @@ def _load_lib():
         "vp_screen_rounds": (U, [P, C.POINTER(C.c_int)]),
         "vp_set_check_order": (U, [P, C.c_int]),
         "vp_check_order": (U, [P, C.POINTER(C.c_int)]),
+        "vp_measure_fp32_peak": (U, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +273,15 @@ def vp_check_order(ctx):
     r = C.c_int(0)
     _check(ctx, lib.vp_check_order(ctx, C.byref(r)))
     return r.value
+
+
+def vp_measure_fp32_peak(device=0, seconds=1.0):
+    """Measured FP32 FMA throughput of `device` (TFLOP/s)."""
+    t = C.c_double(0.0)
+    status = lib.vp_measure_fp32_peak(int(device), C.c_double(seconds), C.byref(t))
+    if status != VP_OK:
+        raise VPError(status, "vp_measure_fp32_peak failed")
+    return t.value
 
 
 def vp_sync_status(ctx, stream=None):

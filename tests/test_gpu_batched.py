@@ -163,6 +163,18 @@ def test_second_phase_matches_plain(vpmod, name, n):
     val.close()
 
 
+def test_measured_fp32_peak(vpmod):
+    """The FMA-chain measurement gives a plausible device rate and rejects
+    bad arguments."""
+    Validator, vp = vpmod
+    t = vp.vp_measure_fp32_peak(0, 0.2)
+    props = torch.cuda.get_device_properties(0)
+    derived_at_3ghz = 2 * 128 * props.multi_processor_count * 3.0e9 / 1e12
+    assert 0.2 * derived_at_3ghz / 3 < t < derived_at_3ghz
+    with pytest.raises(vp.VPError):
+        vp.vp_measure_fp32_peak(0, 0.0)
+
+
 def test_tiling_defaults_then_tuned(vpmod):
     Validator, vp = vpmod
     w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=100_000)

@@ -130,7 +130,8 @@ def test_edges_arm7_every_edge(vpmod):
 
 
 @pytest.mark.parametrize("name,n_sample", [(vpgen.TORSO8_OBB60_CAP20, 768), (vpgen.DUAL14_SHELVES, 512),
-                                           (vpgen.DUAL14_MIXED1000, 256)])
+                                           (vpgen.DUAL14_MIXED1000, 256), (vpgen.DUAL14_SHELVES_FAR, 256),
+                                           (vpgen.DUAL14_MIXED1000_FAR, 256)])
 def test_edges_full_size_sampled(vpmod, name, n_sample):
     """Full-size workloads in the benchmark's launch configuration, checked
     on a seeded sample of edges the oracle classifies one by one."""

@@ -385,10 +385,11 @@ def env_boxes_capsules(seed: int = 101) -> Env:
     return Env(_empty(4), caps, _cuboids(rng, FRONT_BOX, 60, ARM_BASES))
 
 
-def env_shelves(seed: int = 102, n_total: int = 120) -> Env:
+def env_shelves(seed: int = 102, n_total: int = 120, push: float = 0.0) -> Env:
     """Shelf-like scene of oriented cuboids: three shelf units around the
     front of the robot (uprights, back panel, five boards each) and small
-    boxes standing on random boards.  Generated, not taken from any dataset."""
+    boxes standing on random boards.  Generated, not taken from any dataset.
+    ``push`` moves every unit that far further from the robot."""
     rng = np.random.default_rng(seed)
     boxes = []
 
@@ -396,7 +397,7 @@ def env_shelves(seed: int = 102, n_total: int = 120) -> Env:
         R = _yaw_matrices(np.array([yaw]))[0]
         boxes.append(np.concatenate([np.asarray(centre, float), R.reshape(9), np.asarray(half, float)]))
 
-    units = [((0.85, 0.0), 0.0), ((0.2, 0.95), np.pi / 2), ((0.2, -0.95), -np.pi / 2)]
+    units = [((0.85 + push, 0.0), 0.0), ((0.2, 0.95 + push), np.pi / 2), ((0.2, -0.95 - push), -np.pi / 2)]
     depth, width, height = 0.35, 0.9, 1.6
     levels = [0.25, 0.55, 0.85, 1.15, 1.45]
     boards = []
@@ -430,11 +431,13 @@ def env_mixed128(seed: int = 103) -> Env:
     return Env(sph, caps, _cuboids(rng, FRONT_BOX, 32, ARM_BASES))
 
 
-def env_mixed1000(seed: int = 104) -> Env:
+def env_mixed1000(seed: int = 104, shift: float = 0.0) -> Env:
+    """1,000 primitives in the 2 m cube centred at (1 + shift, 0, 1)."""
     rng = np.random.default_rng(seed)
-    sph = _spheres(rng, BIG_BOX, 400, DUAL_BASES)
-    caps = _capsules(rng, BIG_BOX, 300, DUAL_BASES)
-    return Env(sph, caps, _cuboids(rng, BIG_BOX, 300, DUAL_BASES))
+    box = ((BIG_BOX[0][0] + shift, BIG_BOX[0][1] + shift), BIG_BOX[1], BIG_BOX[2])
+    sph = _spheres(rng, box, 400, DUAL_BASES)
+    caps = _capsules(rng, box, 300, DUAL_BASES)
+    return Env(sph, caps, _cuboids(rng, box, 300, DUAL_BASES))
 
 
 # ----------------------------------------------------------------------------
@@ -496,11 +499,21 @@ TORSO8_OBB60_CAP20 = "torso8_obb60_cap20"  # 8-DoF torso arm vs 60 OBBs + 20 cap
 DUAL14_SHELVES = "dual14_shelves"          # 14-DoF dual arm vs 120-cuboid shelves, 262,144 edges
 ARM7_MIXED128 = "arm7_mixed128"            # 7-DoF arm vs 128 mixed primitives, 65,536 configurations
 DUAL14_MIXED1000 = "dual14_mixed1000"      # 14-DoF dual arm vs 1,000 mixed primitives, 4,194,304 edges
-NAMES = (ARM7_SPHERES16, TORSO8_OBB60_CAP20, DUAL14_SHELVES, ARM7_MIXED128, DUAL14_MIXED1000)
+# Obstacle-shifted variants of the two dual-arm workloads (same robot, same
+# edges and counts; only the obstacles move away), added because random
+# edges there are almost all invalid.  Self contact between the two arms
+# already leaves only ~2.7% of those edges collision-free, which bounds any
+# obstacle placement.
+DUAL14_SHELVES_FAR = "dual14_shelves_far"      # shelves pushed 0.6 m further out
+DUAL14_MIXED1000_FAR = "dual14_mixed1000_far"  # the 2 m cube centred 1 m further out
+NAMES = (ARM7_SPHERES16, TORSO8_OBB60_CAP20, DUAL14_SHELVES, ARM7_MIXED128, DUAL14_MIXED1000, DUAL14_SHELVES_FAR,
+         DUAL14_MIXED1000_FAR)
+_VARIANT_OF = {DUAL14_SHELVES_FAR: DUAL14_SHELVES, DUAL14_MIXED1000_FAR: DUAL14_MIXED1000}
 
 #: Full sizes of the five workloads.
 FULL_EDGES = {ARM7_SPHERES16: 10_000, TORSO8_OBB60_CAP20: 1_000_000, DUAL14_SHELVES: 262_144,
-              ARM7_MIXED128: 65_536, DUAL14_MIXED1000: 4_194_304}
+              ARM7_MIXED128: 65_536, DUAL14_MIXED1000: 4_194_304, DUAL14_SHELVES_FAR: 262_144,
+              DUAL14_MIXED1000_FAR: 4_194_304}
 
 DESCRIPTION = {
     ARM7_SPHERES16: "7-DoF arm (40 spheres) vs 16 spheres; 10,000 uniform edges at 1/32 rad",
@@ -511,6 +524,8 @@ DESCRIPTION = {
     ARM7_MIXED128: "7-DoF arm vs 64 spheres + 32 capsules + 32 OBBs; cost at margin 0.02 on 65,536 configurations",
     DUAL14_MIXED1000: "14-DoF dual arm vs 1,000 mixed primitives in a 2 m cube; 4,194,304 edges, counts "
                       "log-uniform in [2,512]",
+    DUAL14_SHELVES_FAR: "dual14_shelves with the shelf units 0.6 m further out (same edges)",
+    DUAL14_MIXED1000_FAR: "dual14_mixed1000 with the 2 m cube centred 1 m further out (same edges)",
 }
 
 # seeds: robots 0/1/2; scenes 100 + index; edges 200 + index (index = position in NAMES)
@@ -522,14 +537,16 @@ def robot_for(name: str) -> Robot:
         return arm7(0, 40)
     if name == TORSO8_OBB60_CAP20:
         return torso_arm8(1, 100, 200)
-    if name in (DUAL14_SHELVES, DUAL14_MIXED1000):
+    if name in (DUAL14_SHELVES, DUAL14_MIXED1000, DUAL14_SHELVES_FAR, DUAL14_MIXED1000_FAR):
         return dual_arm14(60, 400)
     raise ValueError(name)
 
 
 def env_for(name: str) -> Env:
     return {ARM7_SPHERES16: env_spheres16, TORSO8_OBB60_CAP20: env_boxes_capsules, DUAL14_SHELVES: env_shelves,
-            ARM7_MIXED128: env_mixed128, DUAL14_MIXED1000: env_mixed1000}[name]()
+            ARM7_MIXED128: env_mixed128, DUAL14_MIXED1000: env_mixed1000,
+            DUAL14_SHELVES_FAR: lambda: env_shelves(push=0.6),
+            DUAL14_MIXED1000_FAR: lambda: env_mixed1000(shift=1.0)}[name]()
 
 
 def workload(name: str, n_edges: Optional[int] = None, robot: Optional[Robot] = None,
@@ -543,6 +560,10 @@ def workload(name: str, n_edges: Optional[int] = None, robot: Optional[Robot] = 
     robot = robot if robot is not None else robot_for(name)
     env = env if env is not None else env_for(name)
     n = FULL_EDGES[name] if n_edges is None else int(n_edges)
+    if name in _VARIANT_OF:  # the base workload's edges, the variant's obstacles
+        base = workload(_VARIANT_OF[name], n_edges=n, robot=robot, env=env)
+        base.name = name
+        return base
     seed = 200 + _INDEX[name]
     if name in (ARM7_SPHERES16, TORSO8_OBB60_CAP20):
         q0, q1 = uniform_edges(robot, n, seed)
