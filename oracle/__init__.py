@@ -19,6 +19,8 @@ What each function follows in arXiv 2309.14545:
   Euclidean C-space).
 * ``cost`` -- the penetration cost and its gradient, an addition beside the
   paper (no passage defines it).
+* ``oracle.nn.nearest`` -- Sec. "Bringing it Together": l2 nearest neighbours
+  in a Euclidean configuration space, brute force (NumPy, FP64).
 """
 from __future__ import annotations
 
