@@ -429,6 +429,7 @@ def run_native(args):
     if not args.no_compare:
         line["comparisons"] = compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev)
         line["grads"] = grads_leg(dev, flush, stream)
+        line["nearest"] = nn_leg(dev, flush, stream, peak)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
         r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
@@ -505,6 +506,45 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
         vc.close()
         del a, b, c
     return res
+
+
+def nn_leg(dev, flush, stream, peak_tflops):
+    """Batched l2 nearest neighbours (vp_nearest) on uniform configurations
+    in [-2.8, 2.8]^7: a planner-sized batch (1,048,576 tree points, 4,096
+    samples; FP32-bound, 3D flops per pair) and a single query over 4,194,304
+    points (bound by reading the points once from HBM)."""
+    import torch
+    from paper_2309_14545_gb300 import Validator, vp
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=16)
+    v = Validator(w.robot, w.env, device=dev.index)
+    hbm = None
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(9)
+    for name, M, N, D in (("batch", 1 << 20, 4096, 7), ("single_query", 1 << 22, 1, 7)):
+        with torch.cuda.stream(stream):
+            p = torch.rand(M, D, device=dev, generator=g) * 5.6 - 2.8
+            q = torch.rand(N, D, device=dev, generator=g) * 5.6 - 2.8
+            idx = torch.empty(N, dtype=torch.int64, device=dev)
+            d2 = torch.empty(N, dtype=torch.float32, device=dev)
+        med, mn = _timed(lambda: vp.vp_nearest(v.ctx, p, q, idx, d2, stream), flush, stream, 5)
+        rec = {"points": M, "queries": N, "dim": D, "ms": med, "pairs_per_s": M * N / (med / 1e3)}
+        tflops = 3 * D * M * N / (med / 1e3) / 1e12
+        gbs = (M + N) * D * 4 / (med / 1e3) / 1e9
+        if name == "batch":
+            rec["roofline"] = {"bound": "alu", "achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                               "frac": tflops / peak_tflops, "flops_per_pair": 3 * D}
+        else:
+            rec["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": gbs / hbm if hbm else None, "bytes": (M + N) * D * 4,
+                               "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        out[name] = rec
+        del p, q
+    v.close()
+    return out
 
 
 def grads_leg(dev, flush, stream):

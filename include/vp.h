@@ -275,6 +275,21 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
 vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
 
+/* Nearest neighbours in a Euclidean configuration space (Sec. III-E,
+ * "Bringing it Together": the planners' NN structure uses the l2 distance,
+ * a sum of squared coordinate differences).  For each query q_n, the index
+ * of the point p_m with the least d = sum_d (q_n,d - p_m,d)^2, computed in
+ * FP32 in coordinate order (one FMA per coordinate), the lowest index among
+ * equal distances; dist2[n] gets that d.  Brute force over all points.
+ * points: device float [M][D] (1 <= M < 2^32 - 1); queries: device float
+ * [N][D]; 1 <= D <= 16.  index: device int64 [N], 8-byte aligned (also the
+ * call's scratch); dist2: device float [N] or NULL.  A query whose
+ * distances are all non-finite gets index -1.  Needs no robot or
+ * environment; asynchronous on `stream`.  VP_ERR_ARG / VP_ERR_CAPACITY on
+ * bad sizes. */
+vp_status vp_nearest(vp_ctx *ctx, const float *points, int64_t M, const float *queries, int64_t N, int D,
+                     int64_t *index, float *dist2, void *stream);
+
 /* Measured FP32 FMA throughput of CUDA device `device` in TFLOP/s (an FMA is
  * two flops): independent FMA chains on every SM at full occupancy, one
  * launch grown to about seconds / 4, best of three (0 < seconds <= 60; the

@@ -95,6 +95,14 @@ class Validator:
     def set_check_order(self, prims_first):
         vp.vp_set_check_order(self.ctx, prims_first)
 
+    def nearest(self, points, queries, stream=None):
+        """(index int64 [N], squared distance float32 [N]) of each query's
+        l2 nearest neighbour among the points (device float tensors)."""
+        index = torch.empty(queries.shape[0], dtype=torch.int64, device=self._dev())
+        dist2 = torch.empty(queries.shape[0], dtype=torch.float32, device=self._dev())
+        vp.vp_nearest(self.ctx, points, queries, index, dist2, stream)
+        return index, dist2
+
     def collision_cost(self, q, margin, grad=False, stream=None):
         cost = torch.empty(q.shape[0], dtype=torch.float32, device=self._dev())
         g = torch.empty_like(q) if grad else None

@@ -660,6 +660,24 @@ extern "C" vp_status vp_check_order(vp_ctx *ctx, int *prims_first) {
     return VP_OK;
 }
 
+extern "C" vp_status vp_nearest(vp_ctx *ctx, const float *points, int64_t M, const float *queries, int64_t N,
+                                 int D, int64_t *index, float *dist2, void *stream) {
+    if (!ctx) return VP_ERR_ARG;
+    if (D < 1 || D > 16) return fail(ctx, VP_ERR_ARG, "vp_nearest: D must be in [1, 16]");
+    if (M < 1) return fail(ctx, VP_ERR_ARG, "vp_nearest: no points");
+    if (M >= 0xffffffffLL) return fail(ctx, VP_ERR_CAPACITY, "vp_nearest: at most 2^32 - 2 points");
+    if (N < 0) return fail(ctx, VP_ERR_ARG, "vp_nearest: N < 0");
+    if (N == 0) return VP_OK;
+    if (!points || !queries || !index) return fail(ctx, VP_ERR_ARG, "vp_nearest: NULL buffer");
+    if (reinterpret_cast<uintptr_t>(index) % 8) return fail(ctx, VP_ERR_ARG, "vp_nearest: index not 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    std::string msg;
+    const int rc = nn_launch(points, M, queries, N, D, index, dist2, ctx->num_sms, static_cast<cudaStream_t>(stream),
+                             &msg);
+    if (rc == 0) return VP_OK;
+    return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_nearest: %s", msg.c_str());
+}
+
 extern "C" vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits) {
     if (!ctx) return VP_ERR_ARG;
     DeviceGuard g(ctx->device);

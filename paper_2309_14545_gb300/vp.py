@@ -36,7 +36,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
-           "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak")
+           "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest")
 
 
 class VPError(RuntimeError):
@@ -86,6 +86,7 @@ def _load_lib():
         "vp_set_check_order": (U, [P, C.c_int]),
         "vp_check_order": (U, [P, C.POINTER(C.c_int)]),
         "vp_measure_fp32_peak": (U, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
+        "vp_nearest": (U, [P, P, I64, P, I64, C.c_int, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +274,19 @@ def vp_check_order(ctx):
     r = C.c_int(0)
     _check(ctx, lib.vp_check_order(ctx, C.byref(r)))
     return r.value
+
+
+def vp_nearest(ctx, points, queries, index, dist2=None, stream=None):
+    """l2 nearest neighbour of each query among the points (device tensors)."""
+    if points.dim() != 2 or queries.dim() != 2 or points.shape[1] != queries.shape[1]:
+        raise ValueError("points [M, D] and queries [N, D]")
+    M, D = points.shape
+    N = queries.shape[0]
+    _check(ctx, lib.vp_nearest(ctx, _dev(points, torch.float32, "points", (M, D)), M,
+                               _dev(queries, torch.float32, "queries", (N, D)), N, D,
+                               _dev(index, torch.int64, "index", (N,)),
+                               None if dist2 is None else _dev(dist2, torch.float32, "dist2", (N,)),
+                               _stream(stream)))
 
 
 def vp_measure_fp32_peak(device=0, seconds=1.0):
