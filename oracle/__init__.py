@@ -21,6 +21,8 @@ What each function follows in arXiv 2309.14545:
   paper (no passage defines it).
 * ``oracle.nn.nearest`` -- Sec. "Bringing it Together": l2 nearest neighbours
   in a Euclidean configuration space, brute force (NumPy, FP64).
+* ``oracle.shortcut.shortcut`` -- Sec. "Bringing it Together": randomized
+  shortcutting, batched over paths, on the FP64 edge check above.
 """
 from __future__ import annotations
 

@@ -491,6 +491,39 @@ def straight_paths(robot: Robot, n_paths: int, n_way: int, seed: int) -> np.ndar
     return w.astype(np.float32)
 
 
+def jagged_paths(robot: Robot, n_paths: int, n_way: int, seed: int, span: float = 0.5,
+                 noise: float = 0.25) -> np.ndarray:
+    """Jagged joint-space paths, the raw output a sampling planner leaves for
+    shortcutting: ``n_way`` waypoints evenly spaced between random endpoints
+    (drawn within ``span`` of the joint range around its middle), interior
+    waypoints displaced by U[-noise, noise] rad per joint, clipped to the
+    limits.  float32 [n_paths, n_way, D]."""
+    D = robot.dof
+    lo, hi = robot.joint_lo, robot.joint_hi
+    mid, half = 0.5 * (lo + hi), 0.5 * span * (hi - lo)
+    rng = np.random.default_rng([seed, 7])
+    a = mid + half * rng.uniform(-1.0, 1.0, size=(n_paths, D))
+    b = mid + half * rng.uniform(-1.0, 1.0, size=(n_paths, D))
+    s = (np.arange(n_way, dtype=np.float64) / (n_way - 1))[None, :, None]
+    w = a[:, None, :] + s * (b - a)[:, None, :]
+    jitter = rng.uniform(-noise, noise, size=(n_paths, n_way, D))
+    jitter[:, 0] = 0.0
+    jitter[:, -1] = 0.0
+    return np.clip(w + jitter, lo, hi).astype(np.float32)
+
+
+def shortcut_draws(n_iter: int, n_paths: int, seed: int) -> np.ndarray:
+    """The random numbers randomized shortcutting consumes: U[0, 1) float32
+    [n_iter, n_paths, 2] (two waypoint positions per path and iteration)."""
+    rng = np.random.default_rng([seed, 11])
+    return rng.uniform(0.0, 1.0, size=(n_iter, n_paths, 2)).astype(np.float32)
+
+
+#: Shortcutting workload: the 7-DoF arm among the 16-sphere scene
+#: (``arm7_spheres16``), 4,096 jagged paths of 32 waypoints, 64 iterations.
+SHORTCUT_PATHS, SHORTCUT_WAYPOINTS, SHORTCUT_ITERS, SHORTCUT_SEED = 4096, 32, 64, 305
+
+
 # ----------------------------------------------------------------------------
 # the five workloads, by name
 
