@@ -430,6 +430,7 @@ def run_native(args):
         line["comparisons"] = compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev)
         line["grads"] = grads_leg(dev, flush, stream)
         line["nearest"] = nn_leg(dev, flush, stream, peak)
+        line["shortcut"] = shortcut_leg(dev, flush, stream)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
         r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
@@ -543,6 +544,33 @@ def nn_leg(dev, flush, stream, peak_tflops):
                                "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"}
         out[name] = rec
         del p, q
+    v.close()
+    return out
+
+
+def shortcut_leg(dev, flush, stream):
+    """Batched randomized shortcutting: 4,096 jagged 32-waypoint paths of the
+    7-DoF arm among 16 spheres, 64 steps (one batched validation of 4,096
+    candidate shortcuts per step)."""
+    import torch
+    from paper_2309_14545_gb300 import Validator
+    w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=16)
+    v = Validator(w.robot, w.env, device=dev.index)
+    P, W, T = vpgen.SHORTCUT_PATHS, vpgen.SHORTCUT_WAYPOINTS, vpgen.SHORTCUT_ITERS
+    with torch.cuda.stream(stream):
+        paths0 = torch.from_numpy(vpgen.jagged_paths(w.robot, P, W, seed=vpgen.SHORTCUT_SEED)).to(dev)
+        draws = torch.from_numpy(vpgen.shortcut_draws(T, P, seed=vpgen.SHORTCUT_SEED)).to(dev)
+        paths = paths0.clone()
+        lengths = torch.full((P,), W, dtype=torch.int32, device=dev)
+
+    def run():
+        paths.copy_(paths0)
+        lengths.fill_(W)
+        v.shortcut(paths, lengths, draws, float(w.res), stream=stream)
+
+    med, mn = _timed(run, flush, stream, 5)
+    out = {"paths": P, "waypoints": W, "steps": T, "ms": med, "candidates_per_s": P * T / (med / 1e3),
+           "mean_waypoints_after": float(lengths.float().mean().item())}
     v.close()
     return out
 

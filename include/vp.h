@@ -275,6 +275,22 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
 vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
 
+/* Batched randomized shortcutting (Sec. III-E, "Bringing it Together": the
+ * planners simplify paths by randomized shortcutting).  paths: device float
+ * [P][W][D] (D = the robot's joints), in/out; lengths: device int32 [P]
+ * (waypoints in use, 2..W), in/out.  For each of T steps, path p takes the
+ * random numbers (u0, u1) = draws[t][p][0..1] (device float [T][P][2], in
+ * [0, 1)): i = floor(u0 n), j = floor(u1 n) with the products rounded to
+ * float32, clamped to n - 1 and ordered; if n >= 3 and j - i >= 2, the edge
+ * waypoint i -> waypoint j is validated as vp_validate_edges does at
+ * `resolution` (one batched call for all paths per step) and, when valid,
+ * the waypoints strictly between are removed (later ones move up; entries
+ * past the new length are left as they were).  A length outside [3, W]
+ * leaves the path unchanged.  Asynchronous on `stream`; uses a scratch the
+ * context keeps (grown on demand).  Needs a robot and an environment. */
+vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengths, int64_t P, int32_t W, const float *draws,
+                            int32_t T, float resolution, void *stream);
+
 /* Nearest neighbours in a Euclidean configuration space (Sec. III-E,
  * "Bringing it Together": the planners' NN structure uses the l2 distance,
  * a sum of squared coordinate differences).  For each query q_n, the index

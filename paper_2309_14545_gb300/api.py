@@ -95,6 +95,12 @@ class Validator:
     def set_check_order(self, prims_first):
         vp.vp_set_check_order(self.ctx, prims_first)
 
+    def shortcut(self, paths, lengths, draws, resolution=1.0 / 32.0, stream=None):
+        """Randomized shortcutting, in place on device tensors paths
+        [P, W, D] float32 and lengths [P] int32, from draws [T, P, 2]."""
+        vp.vp_shortcut_paths(self.ctx, paths, lengths, draws, resolution, stream)
+        return paths, lengths
+
     def nearest(self, points, queries, stream=None):
         """(index int64 [N], squared distance float32 [N]) of each query's
         l2 nearest neighbour among the points (device float tensors)."""

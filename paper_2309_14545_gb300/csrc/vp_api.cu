@@ -32,6 +32,12 @@ struct vp_ctx {
     bool timing = false;         // record events around the validation kernel
     bool timed = false;          // a timed call has been issued
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    // shortcutting scratch: candidate edges, their waypoint pairs and verdicts
+    float *sc_q0 = nullptr, *sc_q1 = nullptr;
+    int2 *sc_ij = nullptr;
+    uint8_t *sc_ok = nullptr;
+    int64_t sc_cap = 0;
+    int sc_dof = 0;
     std::string err;
 };
 
@@ -121,6 +127,10 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         batched_release(ctx->batched);
         if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
         if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
+        if (ctx->sc_q0) cudaFree(ctx->sc_q0);
+        if (ctx->sc_q1) cudaFree(ctx->sc_q1);
+        if (ctx->sc_ij) cudaFree(ctx->sc_ij);
+        if (ctx->sc_ok) cudaFree(ctx->sc_ok);
     }
     delete ctx;
     return VP_OK;
@@ -657,6 +667,50 @@ extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int prims_first) {
 extern "C" vp_status vp_check_order(vp_ctx *ctx, int *prims_first) {
     if (!ctx || !prims_first) return VP_ERR_ARG;
     *prims_first = batched_check_order(ctx->batched);
+    return VP_OK;
+}
+
+extern "C" vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengths, int64_t P, int32_t W,
+                                        const float *draws, int32_t T, float resolution, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (P < 0 || W < 2 || T < 0) return fail(ctx, VP_ERR_ARG, "vp_shortcut_paths: need P >= 0, W >= 2, T >= 0");
+    if (!(resolution > 0.f) || !std::isfinite(resolution))
+        return fail(ctx, VP_ERR_ARG, "vp_shortcut_paths: resolution must be > 0");
+    if (P == 0 || T == 0) return VP_OK;
+    if (!paths || !lengths || !draws) return fail(ctx, VP_ERR_ARG, "vp_shortcut_paths: NULL buffer");
+    DeviceGuard g(ctx->device);
+    const int D = ctx->robot.n_joints;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (P > ctx->sc_cap || D != ctx->sc_dof) {  // grow the scratch (outside any capture)
+        cudaStreamSynchronize(st);
+        cudaFree(ctx->sc_q0);
+        cudaFree(ctx->sc_q1);
+        cudaFree(ctx->sc_ij);
+        cudaFree(ctx->sc_ok);
+        ctx->sc_q0 = ctx->sc_q1 = nullptr;
+        ctx->sc_ij = nullptr;
+        ctx->sc_ok = nullptr;
+        ctx->sc_cap = 0;
+        e = cudaMalloc(&ctx->sc_q0, P * D * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sc_q1, P * D * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sc_ij, P * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sc_ok, P);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_shortcut_paths (scratch)");
+        ctx->sc_cap = P;
+        ctx->sc_dof = D;
+    }
+    for (int32_t t = 0; t < T; ++t) {
+        e = shortcut_propose(paths, lengths, P, W, D, draws + static_cast<int64_t>(t) * P * 2, ctx->sc_q0,
+                             ctx->sc_q1, ctx->sc_ij, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_shortcut_paths (propose)");
+        s = validate_edges_impl(ctx, ctx->sc_q0, ctx->sc_q1, nullptr, resolution, P, ctx->sc_ok, VP_MODE_BATCHED,
+                                nullptr, stream);
+        if (s != VP_OK) return s;
+        e = shortcut_apply(paths, lengths, P, W, D, ctx->sc_ij, ctx->sc_ok, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_shortcut_paths (apply)");
+    }
     return VP_OK;
 }
 

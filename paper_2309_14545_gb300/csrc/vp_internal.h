@@ -49,6 +49,13 @@ cudaError_t prepare_fk(size_t smem, int block, int *blocks_per_sm);
 cudaError_t launch_counts(int D, const float *q0, const float *q1, float res, int64_t E, int32_t *counts,
                           cudaStream_t st);
 
+// Batched randomized shortcutting (vp_shortcut.cu): the propose and apply
+// steps of one iteration.
+cudaError_t shortcut_propose(const float *paths, const int32_t *lengths, int64_t P, int W, int D, const float *u,
+                             float *q0c, float *q1c, int2 *ij, cudaStream_t st);
+cudaError_t shortcut_apply(float *paths, int32_t *lengths, int64_t P, int W, int D, const int2 *ij, const uint8_t *ok,
+                           cudaStream_t st);
+
 // Batched l2 nearest neighbours (vp_nn.cu); 0 = ok, 1 = capacity, 2 = CUDA error.
 int nn_launch(const float *points, int64_t M, const float *queries, int64_t N, int D, int64_t *index, float *dist2,
               int num_sms, cudaStream_t st, std::string *msg);

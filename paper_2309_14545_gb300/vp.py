@@ -36,7 +36,8 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_validate_states", "vp_edge_counts", "vp_validate_edges", "vp_validate_edges_work",
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
-           "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest")
+           "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest",
+           "vp_shortcut_paths")
 
 
 class VPError(RuntimeError):
@@ -87,6 +88,7 @@ def _load_lib():
         "vp_check_order": (U, [P, C.POINTER(C.c_int)]),
         "vp_measure_fp32_peak": (U, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "vp_nearest": (U, [P, P, I64, P, I64, C.c_int, P, P, P]),
+        "vp_shortcut_paths": (U, [P, P, P, I64, C.c_int32, P, C.c_int32, F, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +289,19 @@ def vp_nearest(ctx, points, queries, index, dist2=None, stream=None):
                                _dev(index, torch.int64, "index", (N,)),
                                None if dist2 is None else _dev(dist2, torch.float32, "dist2", (N,)),
                                _stream(stream)))
+
+
+def vp_shortcut_paths(ctx, paths, lengths, draws, resolution=1.0 / 32.0, stream=None):
+    """Randomized shortcutting in place: paths [P, W, D], lengths [P] int32,
+    draws [T, P, 2] float32 (device tensors)."""
+    if paths.dim() != 3 or draws.dim() != 3:
+        raise ValueError("paths [P, W, D] and draws [T, P, 2]")
+    P_, W, D = paths.shape
+    T = draws.shape[0]
+    _check(ctx, lib.vp_shortcut_paths(ctx, _dev(paths, torch.float32, "paths", (P_, W, D)),
+                                      _dev(lengths, torch.int32, "lengths", (P_,)), P_, W,
+                                      _dev(draws, torch.float32, "draws", (T, P_, 2)), T, C.c_float(resolution),
+                                      _stream(stream)))
 
 
 def vp_measure_fp32_peak(device=0, seconds=1.0):
