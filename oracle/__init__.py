@@ -23,6 +23,9 @@ What each function follows in arXiv 2309.14545:
   in a Euclidean configuration space, brute force (NumPy, FP64).
 * ``oracle.shortcut.shortcut`` -- Sec. "Bringing it Together": randomized
   shortcutting, batched over paths, on the FP64 edge check above.
+* ``oracle.rrt.rrt_connect`` -- Sec. "Bringing it Together": RRT-Connect for
+  one problem, on the FP64 edge check, with float32 nearest-node and
+  steering arithmetic (the decisions the GPU takes in the same precision).
 """
 from __future__ import annotations
 
