@@ -431,6 +431,7 @@ def run_native(args):
         line["grads"] = grads_leg(dev, flush, stream)
         line["nearest"] = nn_leg(dev, flush, stream, peak)
         line["shortcut"] = shortcut_leg(dev, flush, stream)
+        line["rrt_connect"] = rrt_leg(dev, flush, stream)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
         r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
@@ -572,6 +573,38 @@ def shortcut_leg(dev, flush, stream):
     out = {"paths": P, "waypoints": W, "steps": T, "ms": med, "candidates_per_s": P * T / (med / 1e3),
            "mean_waypoints_after": float(lengths.float().mean().item())}
     v.close()
+    return out
+
+
+def rrt_leg(dev, flush, stream):
+    """Batched RRT-Connect: 4,096 problems of the 7-DoF arm among 16
+    spheres and 2,048 of the torso arm among 80 obstacles, 1,024 samples
+    each; one warp per problem, trees on the device."""
+    import torch
+    from paper_2309_14545_gb300 import Validator
+    out = {}
+    for name, B, T, rng, cap in vpgen.RRT_CASES:
+        w = vpgen.workload(name, n_edges=16)
+        v = Validator(w.robot, w.env, device=dev.index)
+        start, goal, samples = vpgen.rrt_problems(w.robot, B, T, seed=vpgen.RRT_SEED)
+        with torch.cuda.stream(stream):
+            s, g, q = (torch.from_numpy(x).to(dev) for x in (start, goal, samples))
+        res = {}
+
+        def run():
+            res.update(v.rrt_connect(s, g, q, rng, float(w.res), cap, stream=stream))
+
+        med, mn = _timed(run, flush, stream, 3)
+        st = res["status"].cpu().numpy()
+        solved = st == 1
+        out[name] = {"problems": B, "samples": T, "range": rng, "cap": cap, "ms": med,
+                     "problems_per_s": B / (med / 1e3), "solved": float(solved.mean()),
+                     "invalid_endpoints": float((st == -1).mean()),
+                     "mean_samples_used_solved": float(res["iters"].cpu().numpy()[solved].mean()) if solved.any()
+                     else None,
+                     "mean_path_waypoints": float(res["path_len"].cpu().numpy()[solved].mean()) if solved.any()
+                     else None}
+        v.close()
     return out
 
 

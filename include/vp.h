@@ -291,6 +291,30 @@ vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
 vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengths, int64_t P, int32_t W, const float *draws,
                             int32_t T, float resolution, void *stream);
 
+/* Batched RRT-Connect (Sec. III-E, "Bringing it Together": RRT-Connect is one
+ * of the planners built on the vectorized primitives), device-resident: B
+ * independent problems (start[b] -> goal[b], device float [B][D]), each
+ * grown from its own random configurations samples[b][0..T) (device float
+ * [B][T][D], the caller's draws):
+ *   trees A (from the start) and B (from the goal); per sample, EXTEND(A):
+ *   the l2-nearest node steps toward the sample by at most `range` (radians;
+ *   the sample itself when within range) and is added if that edge is valid
+ *   (as vp_validate_edges checks it at `resolution`); if not trapped,
+ *   CONNECT(B) extends B toward the new node until it is reached (solved)
+ *   or B is trapped; then A and B swap roles.
+ * Nearest-node distances and steps are FP32 with each operation rounded
+ * separately (no fused multiply-add); ties go to the lowest node index.  A
+ * tree holds at most `cap` nodes (cap >= 2); a full tree is trapped.
+ * Outputs (device int32 unless noted): status[b] = 1 solved, 0 not within T
+ * samples, -1 start or goal invalid; iters[b] = samples used; path: device
+ * float [B][2 cap][D], the solved path start ... goal (path_len[b] rows;
+ * 0 when unsolved); tree_sizes [B][2].  Uses a scratch the context keeps
+ * (grown on demand: B * 2 * cap * (D + 1) * 4 bytes).  The watchdog of
+ * vp_set_watchdog bounds the launch.  Asynchronous on `stream`. */
+vp_status vp_rrt_connect(vp_ctx *ctx, const float *start, const float *goal, int64_t B, const float *samples,
+                         int32_t T, float range, float resolution, int32_t cap, int32_t *status, int32_t *iters,
+                         float *path, int32_t *path_len, int32_t *tree_sizes, void *stream);
+
 /* Nearest neighbours in a Euclidean configuration space (Sec. III-E,
  * "Bringing it Together": the planners' NN structure uses the l2 distance,
  * a sum of squared coordinate differences).  For each query q_n, the index

@@ -101,6 +101,21 @@ class Validator:
         vp.vp_shortcut_paths(self.ctx, paths, lengths, draws, resolution, stream)
         return paths, lengths
 
+    def rrt_connect(self, start, goal, samples, range_=1.0, resolution=1.0 / 32.0, cap=1024, stream=None):
+        """Batched RRT-Connect: one problem per row of start/goal [B, D],
+        samples [B, T, D] (device float tensors).  Returns a dict of device
+        tensors: status, iters, path [B, 2 cap, D], path_len, tree_sizes."""
+        B, D = start.shape
+        dev = self._dev()
+        out = {"status": torch.empty(B, dtype=torch.int32, device=dev),
+               "iters": torch.empty(B, dtype=torch.int32, device=dev),
+               "path": torch.empty((B, 2 * cap, D), dtype=torch.float32, device=dev),
+               "path_len": torch.empty(B, dtype=torch.int32, device=dev),
+               "tree_sizes": torch.empty((B, 2), dtype=torch.int32, device=dev)}
+        vp.vp_rrt_connect(self.ctx, start, goal, samples, range_, resolution, cap, out["status"], out["iters"],
+                          out["path"], out["path_len"], out["tree_sizes"], stream)
+        return out
+
     def nearest(self, points, queries, stream=None):
         """(index int64 [N], squared distance float32 [N]) of each query's
         l2 nearest neighbour among the points (device float tensors)."""

@@ -38,6 +38,10 @@ struct vp_ctx {
     uint8_t *sc_ok = nullptr;
     int64_t sc_cap = 0;
     int sc_dof = 0;
+    // planner scratch: tree nodes and parents, and the problem counter
+    float *rrt_nodes = nullptr;
+    int *rrt_parent = nullptr, *rrt_queue = nullptr;
+    size_t rrt_node_cap = 0, rrt_parent_cap = 0;
     std::string err;
 };
 
@@ -131,6 +135,9 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->sc_q1) cudaFree(ctx->sc_q1);
         if (ctx->sc_ij) cudaFree(ctx->sc_ij);
         if (ctx->sc_ok) cudaFree(ctx->sc_ok);
+        if (ctx->rrt_nodes) cudaFree(ctx->rrt_nodes);
+        if (ctx->rrt_parent) cudaFree(ctx->rrt_parent);
+        if (ctx->rrt_queue) cudaFree(ctx->rrt_queue);
     }
     delete ctx;
     return VP_OK;
@@ -712,6 +719,48 @@ extern "C" vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengt
         if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_shortcut_paths (apply)");
     }
     return VP_OK;
+}
+
+extern "C" vp_status vp_rrt_connect(vp_ctx *ctx, const float *start, const float *goal, int64_t B,
+                                     const float *samples, int32_t T, float range, float resolution, int32_t cap,
+                                     int32_t *status, int32_t *iters, float *path, int32_t *path_len,
+                                     int32_t *tree_sizes, void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (B < 0 || T < 0 || cap < 2) return fail(ctx, VP_ERR_ARG, "vp_rrt_connect: need B >= 0, T >= 0, cap >= 2");
+    if (!(range > 0.f) || !std::isfinite(range) || !(resolution > 0.f) || !std::isfinite(resolution))
+        return fail(ctx, VP_ERR_ARG, "vp_rrt_connect: range and resolution must be > 0");
+    if (B == 0) return VP_OK;
+    if (!start || !goal || (T > 0 && !samples) || !status || !iters || !path || !path_len || !tree_sizes)
+        return fail(ctx, VP_ERR_ARG, "vp_rrt_connect: NULL buffer");
+    if (B > 0x7fffffff) return fail(ctx, VP_ERR_CAPACITY, "vp_rrt_connect: too many problems");
+    DeviceGuard g(ctx->device);
+    const int D = ctx->robot.n_joints;
+    const size_t n_nodes = static_cast<size_t>(B) * 2 * cap * D, n_par = static_cast<size_t>(B) * 2 * cap;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (n_nodes > ctx->rrt_node_cap || n_par > ctx->rrt_parent_cap || !ctx->rrt_queue) {
+        cudaStreamSynchronize(st);
+        cudaFree(ctx->rrt_nodes);
+        cudaFree(ctx->rrt_parent);
+        ctx->rrt_nodes = nullptr;
+        ctx->rrt_parent = nullptr;
+        ctx->rrt_node_cap = ctx->rrt_parent_cap = 0;
+        e = cudaMalloc(&ctx->rrt_nodes, n_nodes * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->rrt_parent, n_par * sizeof(int));
+        if (e == cudaSuccess && !ctx->rrt_queue) e = cudaMalloc(&ctx->rrt_queue, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_rrt_connect (scratch)");
+        ctx->rrt_node_cap = n_nodes;
+        ctx->rrt_parent_cap = n_par;
+    }
+    RRTLaunch L{start, goal, samples, B, T, cap, range, resolution, ctx->rrt_nodes, ctx->rrt_parent, ctx->rrt_queue,
+                status, iters, path, path_len, tree_sizes, ctx->batched.watchdog_ns};
+    EnvView view = ctx->env;
+    view.prims_first = batched_check_order(ctx->batched);
+    std::string msg;
+    const int rc = rrt_launch(ctx->robot, view, L, ctx->status, ctx->num_sms, ctx->smem_optin, st, &msg);
+    if (rc == 0) return VP_OK;
+    return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_rrt_connect: %s", msg.c_str());
 }
 
 extern "C" vp_status vp_nearest(vp_ctx *ctx, const float *points, int64_t M, const float *queries, int64_t N,

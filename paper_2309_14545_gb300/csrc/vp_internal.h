@@ -56,6 +56,22 @@ cudaError_t shortcut_propose(const float *paths, const int32_t *lengths, int64_t
 cudaError_t shortcut_apply(float *paths, int32_t *lengths, int64_t P, int W, int D, const int2 *ij, const uint8_t *ok,
                            cudaStream_t st);
 
+// Batched RRT-Connect (vp_rrt.cu): device buffers of one call.
+struct RRTLaunch {
+    const float *start, *goal, *samples;
+    long long B;
+    int T, cap;
+    float range, res;
+    float *nodes;
+    int *parent, *queue, *status, *iters;
+    float *path;
+    int *path_len, *sizes;
+    unsigned long long watchdog_ns;
+};
+// 0 = ok, 1 = capacity, 2 = CUDA error.
+int rrt_launch(const RobotParams &P, const EnvView &env, const RRTLaunch &L, unsigned *status, int num_sms,
+               size_t smem_optin, cudaStream_t st, std::string *msg);
+
 // Batched l2 nearest neighbours (vp_nn.cu); 0 = ok, 1 = capacity, 2 = CUDA error.
 int nn_launch(const float *points, int64_t M, const float *queries, int64_t N, int D, int64_t *index, float *dist2,
               int num_sms, cudaStream_t st, std::string *msg);

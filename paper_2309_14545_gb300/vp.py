@@ -37,7 +37,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
            "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest",
-           "vp_shortcut_paths")
+           "vp_shortcut_paths", "vp_rrt_connect")
 
 
 class VPError(RuntimeError):
@@ -89,6 +89,7 @@ def _load_lib():
         "vp_measure_fp32_peak": (U, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
         "vp_nearest": (U, [P, P, I64, P, I64, C.c_int, P, P, P]),
         "vp_shortcut_paths": (U, [P, P, P, I64, C.c_int32, P, C.c_int32, F, P]),
+        "vp_rrt_connect": (U, [P, P, P, I64, P, C.c_int32, F, F, C.c_int32, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -302,6 +303,21 @@ def vp_shortcut_paths(ctx, paths, lengths, draws, resolution=1.0 / 32.0, stream=
                                       _dev(lengths, torch.int32, "lengths", (P_,)), P_, W,
                                       _dev(draws, torch.float32, "draws", (T, P_, 2)), T, C.c_float(resolution),
                                       _stream(stream)))
+
+
+def vp_rrt_connect(ctx, start, goal, samples, range_, resolution, cap, status, iters, path, path_len, tree_sizes,
+                   stream=None):
+    """Batched RRT-Connect on device tensors (see include/vp.h)."""
+    B, D = start.shape
+    T = samples.shape[1]
+    _check(ctx, lib.vp_rrt_connect(ctx, _dev(start, torch.float32, "start", (B, D)),
+                                   _dev(goal, torch.float32, "goal", (B, D)), B,
+                                   _dev(samples, torch.float32, "samples", (B, T, D)), T, C.c_float(range_),
+                                   C.c_float(resolution), int(cap), _dev(status, torch.int32, "status", (B,)),
+                                   _dev(iters, torch.int32, "iters", (B,)),
+                                   _dev(path, torch.float32, "path", (B, 2 * cap, D)),
+                                   _dev(path_len, torch.int32, "path_len", (B,)),
+                                   _dev(tree_sizes, torch.int32, "tree_sizes", (B, 2)), _stream(stream)))
 
 
 def vp_measure_fp32_peak(device=0, seconds=1.0):

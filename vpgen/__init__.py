@@ -519,6 +519,25 @@ def shortcut_draws(n_iter: int, n_paths: int, seed: int) -> np.ndarray:
     return rng.uniform(0.0, 1.0, size=(n_iter, n_paths, 2)).astype(np.float32)
 
 
+def rrt_problems(robot: Robot, n_problems: int, n_samples: int, seed: int):
+    """Planning problems for batched RRT-Connect: start and goal uniform in
+    the limits, and each problem's own ``n_samples`` uniform configurations
+    (the random draws the planner consumes).  float32 ([B, D], [B, D],
+    [B, T, D])."""
+    start, goal = uniform_edges(robot, n_problems, seed)
+    D = robot.dof
+    lo, hi = robot.joint_lo, robot.joint_hi
+    rng = np.random.default_rng([seed, 13])
+    samples = (lo + (hi - lo) * rng.uniform(0.0, 1.0, size=(n_problems, n_samples, D))).astype(np.float32)
+    return start, goal, samples
+
+
+#: RRT-Connect workloads: (robot/scene workload, problems, samples each,
+#: range in rad, tree capacity).
+RRT_CASES = (("arm7_spheres16", 4096, 1024, 1.0, 1024),
+             ("torso8_obb60_cap20", 2048, 1024, 0.8, 1024))
+RRT_SEED = 307
+
 #: Shortcutting workload: the 7-DoF arm among the 16-sphere scene
 #: (``arm7_spheres16``), 4,096 jagged paths of 32 waypoints, 64 iterations.
 SHORTCUT_PATHS, SHORTCUT_WAYPOINTS, SHORTCUT_ITERS, SHORTCUT_SEED = 4096, 32, 64, 305
