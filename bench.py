@@ -432,6 +432,7 @@ def run_native(args):
         line["nearest"] = nn_leg(dev, flush, stream, peak)
         line["shortcut"] = shortcut_leg(dev, flush, stream)
         line["rrt_connect"] = rrt_leg(dev, flush, stream)
+        line["fk"] = fk_leg(dev, flush, stream)
     if not args.no_cpu_baseline:
         r, sample, cores, dt = oracle_rate(w, budget_s=args.cpu_budget)
         r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
@@ -605,6 +606,39 @@ def rrt_leg(dev, flush, stream):
                      "mean_path_waypoints": float(res["path_len"].cpu().numpy()[solved].mean()) if solved.any()
                      else None}
         v.close()
+    return out
+
+
+def fk_leg(dev, flush, stream):
+    """Sphere centres of 1,048,576 configurations (vp_fk_spheres): the
+    table-driven kernel against the per-robot kernel generated and compiled
+    at run time (NVRTC).  Bound by writing the centres (HBM)."""
+    import torch
+    from paper_2309_14545_gb300 import Validator, vp
+    hbm = None
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    out = {}
+    for name in (vpgen.ARM7_SPHERES16, vpgen.TORSO8_OBB60_CAP20, vpgen.DUAL14_SHELVES):
+        w = vpgen.workload(name, n_edges=16)
+        v = Validator(w.robot, w.env, device=dev.index)
+        N, S, D = 1 << 20, len(w.robot.sphere_radius), w.robot.dof
+        with torch.cuda.stream(stream):
+            q = torch.from_numpy(vpgen.uniform_configs(w.robot, N, seed=9)).to(dev)
+            c = torch.empty((N, S, 3), dtype=torch.float32, device=dev)
+        rec = {"configs": N, "spheres": S, "bytes": N * (D + 3 * S) * 4}
+        for tag, gen in (("table", False), ("generated", True)):
+            if gen:
+                rec["compile_ms"] = v.fk_codegen(True)
+            med, mn = _timed(lambda: vp.vp_fk_spheres(v.ctx, q, c, stream), flush, stream, 5)
+            gbs = rec["bytes"] / (med / 1e3) / 1e9
+            rec[tag] = {"ms": med, "configs_per_s": N / (med / 1e3),
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                     "frac": gbs / hbm if hbm else None}}
+        v.close()
+        out[name] = rec
     return out
 
 

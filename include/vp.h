@@ -291,6 +291,19 @@ vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
 vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengths, int64_t P, int32_t W, const float *draws,
                             int32_t T, float resolution, void *stream);
 
+/* Per-robot forward kinematics by code generation (Sec. III-B: the paper's
+ * tracing compiler turns the robot's kinematics into straight-line code with
+ * its constants folded in).  enable != 0: generate a CUDA kernel for the
+ * loaded robot (every joint and sphere unrolled, fixed transforms and sphere
+ * offsets as literals, zero terms dropped), compile it with NVRTC for the
+ * current device (the first time), and make vp_fk_spheres use it; it
+ * computes what the table-driven kernel computes, in the same order of
+ * operations.  enable == 0: back to the table-driven kernel.  Loading a
+ * robot drops the generated kernel.  *compile_ms (may be NULL) gets the
+ * generation and compile time.  VP_ERR_CUDA (and the table-driven kernel
+ * stays in use) when NVRTC is missing or compilation fails. */
+vp_status vp_fk_codegen(vp_ctx *ctx, int enable, double *compile_ms);
+
 /* Batched RRT-Connect (Sec. III-E, "Bringing it Together": RRT-Connect is one
  * of the planners built on the vectorized primitives), device-resident: B
  * independent problems (start[b] -> goal[b], device float [B][D]), each

@@ -116,6 +116,11 @@ class Validator:
                           out["path"], out["path_len"], out["tree_sizes"], stream)
         return out
 
+    def fk_codegen(self, enable=True):
+        """Use (or stop using) the per-robot FK kernel generated and compiled
+        at run time for fk_spheres; returns the compile time in ms."""
+        return vp.vp_fk_codegen(self.ctx, enable)
+
     def nearest(self, points, queries, stream=None):
         """(index int64 [N], squared distance float32 [N]) of each query's
         l2 nearest neighbour among the points (device float tensors)."""

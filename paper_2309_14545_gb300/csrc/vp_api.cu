@@ -42,6 +42,8 @@ struct vp_ctx {
     float *rrt_nodes = nullptr;
     int *rrt_parent = nullptr, *rrt_queue = nullptr;
     size_t rrt_node_cap = 0, rrt_parent_cap = 0;
+    FkCodegen fk_gen;            // per-robot FK compiled at run time (vp_fk_codegen)
+    bool fk_gen_on = false;
     std::string err;
 };
 
@@ -138,6 +140,7 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->rrt_nodes) cudaFree(ctx->rrt_nodes);
         if (ctx->rrt_parent) cudaFree(ctx->rrt_parent);
         if (ctx->rrt_queue) cudaFree(ctx->rrt_queue);
+        fk_codegen_release(&ctx->fk_gen);
     }
     delete ctx;
     return VP_OK;
@@ -344,6 +347,11 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     ctx->sorted_of = sorted_of;
     ctx->robot_loaded = true;
     batched_invalidate(ctx->batched);
+    {  // a generated FK belongs to the previous robot
+        DeviceGuard g(ctx->device);
+        fk_codegen_release(&ctx->fk_gen);
+        ctx->fk_gen_on = false;
+    }
     return VP_OK;
 }
 
@@ -435,8 +443,14 @@ extern "C" vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float
     if (n == 0) return VP_OK;
     if (!q || !centres) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
-    const int block = 128;
-    const size_t smem = static_cast<size_t>(ctx->robot.n_slots) * kFrameFloats * block * sizeof(float);
+    if (ctx->fk_gen_on) {
+        const cudaError_t e =
+            fk_codegen_launch(ctx->fk_gen, ctx->robot.n_spheres, q, n, centres, static_cast<cudaStream_t>(stream));
+        return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_fk_spheres (generated)");
+    }
+    const int block = fk_configs_per_block(ctx->robot.n_spheres);
+    const size_t smem = (static_cast<size_t>(ctx->robot.n_slots) * kFrameFloats + 3 * ctx->robot.n_spheres) * block *
+                        sizeof(float);
     int bps = 0;
     cudaError_t e = prepare_fk(smem, block, &bps);
     if (e == cudaSuccess) {
@@ -761,6 +775,23 @@ extern "C" vp_status vp_rrt_connect(vp_ctx *ctx, const float *start, const float
     const int rc = rrt_launch(ctx->robot, view, L, ctx->status, ctx->num_sms, ctx->smem_optin, st, &msg);
     if (rc == 0) return VP_OK;
     return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_rrt_connect: %s", msg.c_str());
+}
+
+extern "C" vp_status vp_fk_codegen(vp_ctx *ctx, int enable, double *compile_ms) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "robot not loaded");
+    DeviceGuard g(ctx->device);
+    if (!enable) {
+        ctx->fk_gen_on = false;
+        return VP_OK;
+    }
+    if (!ctx->fk_gen.kernel) {
+        std::string msg;
+        if (fk_codegen_build(ctx->robot, &ctx->fk_gen, &msg) != 0) return fail(ctx, VP_ERR_CUDA, "vp_fk_codegen: %s", msg.c_str());
+    }
+    ctx->fk_gen_on = true;
+    if (compile_ms) *compile_ms = ctx->fk_gen.compile_ms;
+    return VP_OK;
 }
 
 extern "C" vp_status vp_nearest(vp_ctx *ctx, const float *points, int64_t M, const float *queries, int64_t N,

@@ -45,6 +45,7 @@ cudaError_t prepare_states(int lmax, size_t smem, int block, int *blocks_per_sm)
 cudaError_t launch_fk(const RobotParams &P, const float *q, int64_t N, float *centres, int grid, int block,
                       size_t smem, cudaStream_t st);
 cudaError_t prepare_fk(size_t smem, int block, int *blocks_per_sm);
+int fk_configs_per_block(int n_spheres);
 
 cudaError_t launch_counts(int D, const float *q0, const float *q1, float res, int64_t E, int32_t *counts,
                           cudaStream_t st);
@@ -55,6 +56,19 @@ cudaError_t shortcut_propose(const float *paths, const int32_t *lengths, int64_t
                              float *q0c, float *q1c, int2 *ij, cudaStream_t st);
 cudaError_t shortcut_apply(float *paths, int32_t *lengths, int64_t P, int W, int D, const int2 *ij, const uint8_t *ok,
                            cudaStream_t st);
+
+// Per-robot FK compiled at run time (vp_codegen.cu).
+struct FkCodegen {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+    size_t source_bytes = 0;
+    double compile_ms = 0.0;
+};
+std::string fk_source(const RobotParams &P);
+int fk_codegen_build(const RobotParams &P, FkCodegen *out, std::string *msg);  // 0 = ok, 2 = failure
+void fk_codegen_release(FkCodegen *g);
+cudaError_t fk_codegen_launch(const FkCodegen &g, int n_spheres, const float *q, int64_t N, float *centres,
+                              cudaStream_t st);
 
 // Batched RRT-Connect (vp_rrt.cu): device buffers of one call.
 struct RRTLaunch {

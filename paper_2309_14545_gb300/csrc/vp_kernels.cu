@@ -40,43 +40,55 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) states_kernel(const __grid_constan
     }
 }
 
-// FK sphere centres: one thread per configuration.
-__global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
-                                                 const long long N, float *__restrict__ out) {
+// FK sphere centres: one thread per configuration, a block of kFkConfigs
+// consecutive configurations.  The centres go to shared memory first (in the
+// caller's sphere order), then the block writes its configurations' rows as
+// one contiguous, coalesced stream.
+__global__ void __launch_bounds__(32) fk_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
+                                                const long long N, float *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int cpb = blockDim.x;
+    const int D = P.n_joints, S = P.n_spheres;
+    float *buf = reinterpret_cast<float *>(smem);  // [cpb][3 S]
     Stash stash;
-    stash.frames = reinterpret_cast<float *>(smem);
+    stash.frames = buf + static_cast<size_t>(cpb) * 3 * S;
     stash.centres = nullptr;
     stash.motion = nullptr;
-    stash.stride = static_cast<int>(blockDim.x);
-    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int D = P.n_joints, S = P.n_spheres;
-    const float *qi = q + i * D;
-    float *oi = out + i * 3 * S;
-    Fr f;
-    fr_identity(f);
-    for (int l = 0; l <= D; ++l) {
-        if (l > 0) {
-            const JointC &J = P.joints[l - 1];
-            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
-            if (pm == kParentBase)
-                fr_identity(f);
-            else if (pm != kParentPrev)
-                stash.load_frame(pm, f);
-            apply_joint(J, qi[l - 1], f);
-            if (P.links[l].slot >= 0) stash.store_frame(P.links[l].slot, f);
-        }
-        const LinkC &L = P.links[l];
-        for (int s = L.s0; s < L.s1; ++s) {
-            const float4 sp = P.spheres[s];
-            const float3 c = fr_apply(f, sp.x, sp.y, sp.z);
-            float *o = oi + 3 * P.perm[s];
-            o[0] = c.x;
-            o[1] = c.y;
-            o[2] = c.z;
+    stash.stride = cpb;
+    const long long base = static_cast<long long>(blockIdx.x) * cpb;
+    const long long i = base + threadIdx.x;
+    if (i < N) {
+        const float *qi = q + i * D;
+        float *oi = buf + static_cast<size_t>(threadIdx.x) * 3 * S;
+        Fr f;
+        fr_identity(f);
+        for (int l = 0; l <= D; ++l) {
+            if (l > 0) {
+                const JointC &J = P.joints[l - 1];
+                const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+                if (pm == kParentBase)
+                    fr_identity(f);
+                else if (pm != kParentPrev)
+                    stash.load_frame(pm, f);
+                apply_joint(J, qi[l - 1], f);
+                if (P.links[l].slot >= 0) stash.store_frame(P.links[l].slot, f);
+            }
+            const LinkC &L = P.links[l];
+            for (int s = L.s0; s < L.s1; ++s) {
+                const float4 sp = P.spheres[s];
+                const float3 c = fr_apply(f, sp.x, sp.y, sp.z);
+                float *o = oi + 3 * P.perm[s];
+                o[0] = c.x;
+                o[1] = c.y;
+                o[2] = c.z;
+            }
         }
     }
+    __syncthreads();
+    const long long rows = min(static_cast<long long>(cpb), N - base);
+    const long long count = rows * 3 * S;
+    float *dst = out + base * 3 * S;
+    for (long long e = threadIdx.x; e < count; e += cpb) dst[e] = buf[e];
 }
 
 __global__ void counts_kernel(const int D, const float *__restrict__ q0, const float *__restrict__ q1,
@@ -139,6 +151,14 @@ cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float 
 
 cudaError_t prepare_fk(size_t smem, int block, int *blocks_per_sm) {
     return prepare(fk_kernel, smem, block, blocks_per_sm);
+}
+
+// Configurations per FK block: 32 while a block's output rows fit in 48 KB
+// of shared memory, else fewer.
+int fk_configs_per_block(int n_spheres) {
+    int c = 32;
+    while (c > 4 && static_cast<size_t>(c) * 3 * n_spheres * sizeof(float) > 48 * 1024) c /= 2;
+    return c;
 }
 
 cudaError_t launch_fk(const RobotParams &P, const float *q, int64_t N, float *centres, int grid, int block,

@@ -37,7 +37,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
            "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest",
-           "vp_shortcut_paths", "vp_rrt_connect")
+           "vp_shortcut_paths", "vp_rrt_connect", "vp_fk_codegen")
 
 
 class VPError(RuntimeError):
@@ -90,6 +90,7 @@ def _load_lib():
         "vp_nearest": (U, [P, P, I64, P, I64, C.c_int, P, P, P]),
         "vp_shortcut_paths": (U, [P, P, P, I64, C.c_int32, P, C.c_int32, F, P]),
         "vp_rrt_connect": (U, [P, P, P, I64, P, C.c_int32, F, F, C.c_int32, P, P, P, P, P, P]),
+        "vp_fk_codegen": (U, [P, C.c_int, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -318,6 +319,14 @@ def vp_rrt_connect(ctx, start, goal, samples, range_, resolution, cap, status, i
                                    _dev(path, torch.float32, "path", (B, 2 * cap, D)),
                                    _dev(path_len, torch.int32, "path_len", (B,)),
                                    _dev(tree_sizes, torch.int32, "tree_sizes", (B, 2)), _stream(stream)))
+
+
+def vp_fk_codegen(ctx, enable=True):
+    """Switch vp_fk_spheres to (or from) the per-robot generated kernel;
+    returns the generation and compile time in ms."""
+    ms = C.c_double(0.0)
+    _check(ctx, lib.vp_fk_codegen(ctx, int(bool(enable)), C.byref(ms)))
+    return ms.value
 
 
 def vp_measure_fp32_peak(device=0, seconds=1.0):
