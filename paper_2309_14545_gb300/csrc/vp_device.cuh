@@ -46,6 +46,11 @@ __device__ __forceinline__ float3 fr_apply(const Fr &f, float x, float y, float 
                        fmaf(f.r3, x, fmaf(f.r4, y, fmaf(f.r5, z, f.py))),
                        fmaf(f.r6, x, fmaf(f.r7, y, fmaf(f.r8, z, f.pz))));
 }
+// R^T v: a world direction in the frame's coordinates.
+__device__ __forceinline__ float3 fr_unrotate(const Fr &f, float x, float y, float z) {
+    return make_float3(fmaf(f.r0, x, fmaf(f.r3, y, f.r6 * z)), fmaf(f.r1, x, fmaf(f.r4, y, f.r7 * z)),
+                       fmaf(f.r2, x, fmaf(f.r5, y, f.r8 * z)));
+}
 
 // The joint's motion parameters: (sin q, cos q) for a revolute joint, (q, 0)
 // for a prismatic one.
@@ -415,6 +420,11 @@ template <>
 struct Kind<0> {
     static constexpr int kWords = 1, kCoarse = VP_WORK_COARSE_SPHERE, kFine = VP_WORK_FINE_SPHERE;
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) { return hit_sphere(c, r, o[0]); }
+    // the primitive in the coordinates of frame f (x_local = R^T (x - p))
+    __device__ static __forceinline__ void to_frame(const Fr &f, const float4 *o, float4 *ol) {
+        const float3 c = fr_unrotate(f, o[0].x - f.px, o[0].y - f.py, o[0].z - f.pz);
+        ol[0] = make_float4(c.x, c.y, c.z, o[0].w);
+    }
 };
 template <>
 struct Kind<1> {
@@ -422,12 +432,27 @@ struct Kind<1> {
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
         return hit_capsule(c, r, o[0], o[1]);
     }
+    __device__ static __forceinline__ void to_frame(const Fr &f, const float4 *o, float4 *ol) {
+        const float3 a = fr_unrotate(f, o[0].x - f.px, o[0].y - f.py, o[0].z - f.pz);
+        const float3 u = fr_unrotate(f, o[1].x, o[1].y, o[1].z);
+        ol[0] = make_float4(a.x, a.y, a.z, o[0].w);
+        ol[1] = make_float4(u.x, u.y, u.z, o[1].w);
+    }
 };
 template <>
 struct Kind<2> {
     static constexpr int kWords = 4, kCoarse = VP_WORK_COARSE_CUBOID, kFine = VP_WORK_FINE_CUBOID;
     __device__ static __forceinline__ bool hit(float3 c, float r, const float4 *o) {
         return hit_cuboid(c, r, o[0], o[1], o[2], o[3]);
+    }
+    // axis a_i -> R^T a_i; offset -a_i . c -> a_i . p - a_i . c (the same planes)
+    __device__ static __forceinline__ void to_frame(const Fr &f, const float4 *o, float4 *ol) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float3 a = fr_unrotate(f, o[i].x, o[i].y, o[i].z);
+            ol[i] = make_float4(a.x, a.y, a.z, fmaf(o[i].x, f.px, fmaf(o[i].y, f.py, fmaf(o[i].z, f.pz, o[i].w))));
+        }
+        ol[3] = o[3];
     }
 };
 
@@ -524,10 +549,12 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                 if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
                 const bool h = (bits >> l) & 1u;
                 if (h) w.add(VP_WORK_FINE_OWN, L.s1 - L.s0);
+                float4 ol[K::kWords];  // the primitive in the link's frame: spheres tested in local coordinates
+                K::to_frame(f, o, ol);
 #pragma unroll 1
                 for (int s = L.s0; s < L.s1; ++s) {
                     const float4 sp = P.spheres[s];
-                    col |= h && K::hit(fr_apply(f, sp.x, sp.y, sp.z), sp.w, o);
+                    col |= h && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
                 }
                 if (group_stop<MODE>(ctl, col)) return true;
             }
