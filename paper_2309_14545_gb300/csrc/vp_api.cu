@@ -213,6 +213,37 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         order[s] = s;
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return r->sphere_link[a] < r->sphere_link[b]; });
+    // within a link of 4 or more spheres: along the principal axis of their
+    // centres, so the first and second halves are compact (each gets its own
+    // bounding sphere below)
+    for (int i = 0; i < S;) {
+        const int l = r->sphere_link[order[i]];
+        int j = i;
+        while (j < S && r->sphere_link[order[j]] == l) ++j;
+        if (j - i >= 4) {
+            double m[3] = {0, 0, 0}, C[3][3] = {{0}};
+            for (int k = i; k < j; ++k)
+                for (int a = 0; a < 3; ++a) m[a] += r->sphere_centre[3 * order[k] + a] / (j - i);
+            for (int k = i; k < j; ++k)
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        C[a][b] += (r->sphere_centre[3 * order[k] + a] - m[a]) * (r->sphere_centre[3 * order[k] + b] - m[b]);
+            double u[3] = {C[0][0] + 1e-12, C[1][1] + 2e-12, C[2][2] + 3e-12};  // power iteration
+            for (int it = 0; it < 64; ++it) {
+                double v[3];
+                for (int a = 0; a < 3; ++a) v[a] = C[a][0] * u[0] + C[a][1] * u[1] + C[a][2] * u[2];
+                const double n = norm3(v);
+                if (!(n > 0)) break;
+                for (int a = 0; a < 3; ++a) u[a] = v[a] / n;
+            }
+            auto proj = [&](int s) {
+                const double *p = r->sphere_centre + 3 * s;
+                return p[0] * u[0] + p[1] * u[1] + p[2] * u[2];
+            };
+            std::stable_sort(order.begin() + i, order.begin() + j, [&](int a, int b) { return proj(a) < proj(b); });
+        }
+        i = j;
+    }
     std::vector<uint16_t> sorted_of(S);
     for (int i = 0; i < S; ++i) {
         const int s = order[i];
@@ -228,6 +259,9 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         K.s0 = K.s1 = 0;
         K.g0 = K.g1 = 0;
         K.bs = float4{0.f, 0.f, 0.f, -1.f};
+        K.sm = 0;
+        K.pad = 0;
+        rp.halves[l][0] = rp.halves[l][1] = float4{0.f, 0.f, 0.f, -1.f};
     }
     for (int i = 0; i < S;) {
         const int l = r->sphere_link[order[i]];
@@ -235,7 +269,28 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         while (j < S && r->sphere_link[order[j]] == l) ++j;
         rp.links[l].s0 = static_cast<int16_t>(i);
         rp.links[l].s1 = static_cast<int16_t>(j);
+        rp.links[l].sm = static_cast<int16_t>(j - i >= 4 ? i + (j - i) / 2 : j);
         i = j;
+    }
+    // bounding spheres of the halves (mean centre, radius + eps)
+    auto half_sphere = [&](int a, int b) {
+        double c[3] = {0, 0, 0}, R = 0;
+        for (int k = a; k < b; ++k)
+            for (int d = 0; d < 3; ++d) c[d] += r->sphere_centre[3 * order[k] + d] / (b - a);
+        for (int k = a; k < b; ++k) {
+            const double *p = r->sphere_centre + 3 * order[k];
+            const double d3[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+            R = std::max(R, norm3(d3) + r->sphere_radius[order[k]]);
+        }
+        return float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
+                      static_cast<float>(R) + kCoarseEps};
+    };
+    for (int l = 0; l < L; ++l) {
+        LinkC &K = rp.links[l];
+        if (K.sm < K.s1) {
+            rp.halves[l][0] = half_sphere(K.s0, K.sm);
+            rp.halves[l][1] = half_sphere(K.sm, K.s1);
+        }
     }
 
     // link bounding spheres (Sec. III-D mid-phase): given and checked, or derived
@@ -347,11 +402,11 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
     ctx->sorted_of = sorted_of;
     ctx->robot_loaded = true;
     batched_invalidate(ctx->batched);
-    {  // a generated FK belongs to the previous robot
+    if (ctx->fk_gen.kernel) {  // a generated FK belongs to the previous robot
         DeviceGuard g(ctx->device);
         fk_codegen_release(&ctx->fk_gen);
-        ctx->fk_gen_on = false;
     }
+    ctx->fk_gen_on = false;
     return VP_OK;
 }
 

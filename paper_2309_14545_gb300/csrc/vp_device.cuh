@@ -545,16 +545,28 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                 any &= any - 1;
                 const LinkC &L = P.links[l];
                 const Fr &f = frame_at<SIMPLE>(P, l, stash, fc);
-                w.slot(VP_WORK_LANE_FINE, L.s1 - L.s0);
-                if (!ctl.idle) w.add(K::kFine, L.s1 - L.s0);
                 const bool h = (bits >> l) & 1u;
-                if (h) w.add(VP_WORK_FINE_OWN, L.s1 - L.s0);
                 float4 ol[K::kWords];  // the primitive in the link's frame: spheres tested in local coordinates
                 K::to_frame(f, o, ol);
+                // a link split in halves: each half's bounding sphere first; a
+                // half no lane touches is skipped by the whole warp
+                int a0 = L.s0, a1 = L.s1;
+                bool hA = h, hB = h;
+                if (L.sm < L.s1) {
+                    const float4 g0 = P.halves[l][0], g1 = P.halves[l][1];
+                    hA = h && K::hit(make_float3(g0.x, g0.y, g0.z), g0.w, ol);
+                    hB = h && K::hit(make_float3(g1.x, g1.y, g1.z), g1.w, ol);
+                    if (!ctl.idle) w.add(K::kCoarse, 2);
+                    if (!__any_sync(kFull, hA)) a0 = L.sm;
+                    if (!__any_sync(kFull, hB)) a1 = L.sm;
+                }
+                w.slot(VP_WORK_LANE_FINE, a1 - a0);
+                if (!ctl.idle) w.add(K::kFine, a1 - a0);
+                if (STATS) w.add(VP_WORK_FINE_OWN, (hA ? max(0, L.sm - a0) : 0) + (hB ? max(0, a1 - L.sm) : 0));
 #pragma unroll 1
-                for (int s = L.s0; s < L.s1; ++s) {
+                for (int s = a0; s < a1; ++s) {
                     const float4 sp = P.spheres[s];
-                    col |= h && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
+                    col |= (s < L.sm ? hA : hB) && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
                 }
                 if (group_stop<MODE>(ctl, col)) return true;
             }

@@ -51,7 +51,9 @@ struct LinkC {  // 32 bytes
     int16_t g0, g1;  // self groups [g0, g1) checked once this link is posed
     int16_t slot;    // frame-stash slot (branch point; FK and cost kernels), -1 if none
     uint16_t path;   // joints from the base to this link (bit j = joint j)
-    int16_t pad[2];
+    int16_t sm;      // the spheres split in halves [s0, sm), [sm, s1) (sm == s1: not split);
+                     // RobotParams::halves holds their bounding spheres
+    int16_t pad;
 };
 
 struct GroupC {      // one link pair (la <= lb) and its sphere pairs
@@ -71,6 +73,7 @@ struct RobotParams {
     int simple;          // 1: canonical axes and identity origin rotations only
     JointC joints[kMaxJoints];
     LinkC links[kMaxLinks];
+    float4 halves[kMaxLinks][2];  // bounding spheres of a split link's halves (link frame, radius + eps)
     float4 spheres[kMaxSpheres];  // local centre, radius (sorted by link)
     GroupC groups[kMaxGroups];
     PairC pairs[kMaxPairs];
