@@ -556,6 +556,7 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                     const float4 g0 = P.halves[l][0], g1 = P.halves[l][1];
                     hA = h && K::hit(make_float3(g0.x, g0.y, g0.z), g0.w, ol);
                     hB = h && K::hit(make_float3(g1.x, g1.y, g1.z), g1.w, ol);
+                    w.slot(VP_WORK_LANE_COARSE, 2);
                     if (!ctl.idle) w.add(K::kCoarse, 2);
                     if (!__any_sync(kFull, hA)) a0 = L.sm;
                     if (!__any_sync(kFull, hB)) a1 = L.sm;
