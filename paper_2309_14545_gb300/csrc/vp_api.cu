@@ -272,16 +272,41 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         rp.links[l].sm = static_cast<int16_t>(j - i >= 4 ? i + (j - i) / 2 : j);
         i = j;
     }
-    // bounding spheres of the halves (mean centre, radius + eps)
-    auto half_sphere = [&](int a, int b) {
-        double c[3] = {0, 0, 0}, R = 0;
-        for (int k = a; k < b; ++k)
-            for (int d = 0; d < 3; ++d) c[d] += r->sphere_centre[3 * order[k] + d] / (b - a);
+    // bounding sphere of the sorted spheres [a, b) in their link's frame: of
+    // two centres (the mean of the centres, and the middle of the box around
+    // the spheres) the one that needs the smaller radius.  Neither is the
+    // minimal sphere, but both enclose every sphere exactly in double
+    // precision; the float radius gets kCoarseEps on top.
+    auto bound_spheres = [&](int a, int b, double c[3]) {
+        double m[3] = {0, 0, 0}, lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) lo[d] = HUGE_VAL, hi[d] = -HUGE_VAL;
         for (int k = a; k < b; ++k) {
             const double *p = r->sphere_centre + 3 * order[k];
-            const double d3[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
-            R = std::max(R, norm3(d3) + r->sphere_radius[order[k]]);
+            const double rad = r->sphere_radius[order[k]];
+            for (int d = 0; d < 3; ++d) {
+                m[d] += p[d] / (b - a);
+                lo[d] = std::min(lo[d], p[d] - rad);
+                hi[d] = std::max(hi[d], p[d] + rad);
+            }
         }
+        auto radius_about = [&](const double *q) {
+            double R = 0;
+            for (int k = a; k < b; ++k) {
+                const double *p = r->sphere_centre + 3 * order[k];
+                const double d3[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+                R = std::max(R, norm3(d3) + r->sphere_radius[order[k]]);
+            }
+            return R;
+        };
+        const double mid[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+        const double Rm = radius_about(m), Rb = radius_about(mid);
+        const double *best = Rb < Rm ? mid : m;
+        for (int d = 0; d < 3; ++d) c[d] = best[d];
+        return std::min(Rm, Rb);
+    };
+    auto half_sphere = [&](int a, int b) {
+        double c[3];
+        const double R = bound_spheres(a, b, c);
         return float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
                       static_cast<float>(R) + kCoarseEps};
     };
@@ -293,34 +318,31 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         }
     }
 
-    // link bounding spheres (Sec. III-D mid-phase): given and checked, or derived
+    // link bounding spheres (Sec. III-D mid-phase): a given sphere is checked
+    // to contain its link's spheres; the derived bound replaces it where that
+    // is tighter (the hierarchy only culls, so any enclosing sphere gives the
+    // same verdicts)
     for (int l = 0; l < L; ++l) {
         LinkC &K = rp.links[l];
         if (K.s0 == K.s1) continue;
-        double c[3] = {0, 0, 0}, R = 0;
+        double c[3];
+        double R = bound_spheres(K.s0, K.s1, c);
         if (r->link_spheres) {
             const double *g = r->link_spheres + 4 * l;
             if (!finite_all(g, 4)) return fail(ctx, VP_ERR_ARG, "link sphere %d is not finite", l);
-            c[0] = g[0];
-            c[1] = g[1];
-            c[2] = g[2];
-            R = g[3];
-        } else {
-            for (int i = K.s0; i < K.s1; ++i)
-                for (int a = 0; a < 3; ++a) c[a] += r->sphere_centre[3 * order[i] + a];
-            for (int a = 0; a < 3; ++a) c[a] /= (K.s1 - K.s0);
-        }
-        double need = 0;
-        for (int i = K.s0; i < K.s1; ++i) {
-            const double *p = r->sphere_centre + 3 * order[i];
-            const double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
-            need = std::max(need, norm3(d) + r->sphere_radius[order[i]]);
-        }
-        if (r->link_spheres) {
-            if (need > R + 1e-9)
-                return fail(ctx, VP_ERR_ARG, "link sphere %d does not contain its spheres (needs %.6g > %.6g)", l, need, R);
-        } else {
-            R = need;
+            double need = 0;
+            for (int i = K.s0; i < K.s1; ++i) {
+                const double *p = r->sphere_centre + 3 * order[i];
+                const double d[3] = {p[0] - g[0], p[1] - g[1], p[2] - g[2]};
+                need = std::max(need, norm3(d) + r->sphere_radius[order[i]]);
+            }
+            if (need > g[3] + 1e-9)
+                return fail(ctx, VP_ERR_ARG, "link sphere %d does not contain its spheres (needs %.6g > %.6g)", l, need,
+                            g[3]);
+            if (g[3] <= R) {
+                for (int d = 0; d < 3; ++d) c[d] = g[d];
+                R = g[3];
+            }
         }
         K.bs = float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
                       static_cast<float>(R) + kCoarseEps};
