@@ -269,15 +269,17 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         while (j < S && r->sphere_link[order[j]] == l) ++j;
         rp.links[l].s0 = static_cast<int16_t>(i);
         rp.links[l].s1 = static_cast<int16_t>(j);
-        rp.links[l].sm = static_cast<int16_t>(j - i >= 4 ? i + (j - i) / 2 : j);
+        rp.links[l].sm = static_cast<int16_t>(j);
         i = j;
     }
-    // bounding sphere of the sorted spheres [a, b) in their link's frame: of
-    // two centres (the mean of the centres, and the middle of the box around
-    // the spheres) the one that needs the smaller radius.  Neither is the
-    // minimal sphere, but both enclose every sphere exactly in double
-    // precision; the float radius gets kCoarseEps on top.
-    auto bound_spheres = [&](int a, int b, double c[3]) {
+    // bounding sphere of the sorted spheres [a, b) in their link's frame:
+    // start from the better of two centres (the mean of the centres, the
+    // middle of the box around the spheres), then take Badoiu-Clarkson steps
+    // (move the centre 1/(k+1) of the way to the farthest surface point) and
+    // keep the best centre seen.  The radius is recomputed exactly for each
+    // centre, so the sphere encloses every sphere in double precision; the
+    // float radius gets kCoarseEps on top.
+    auto bound_spheres = [&](int a, int b, double c[3], int steps = 256) {
         double m[3] = {0, 0, 0}, lo[3], hi[3];
         for (int d = 0; d < 3; ++d) lo[d] = HUGE_VAL, hi[d] = -HUGE_VAL;
         for (int k = a; k < b; ++k) {
@@ -301,8 +303,30 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         const double mid[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
         const double Rm = radius_about(m), Rb = radius_about(mid);
         const double *best = Rb < Rm ? mid : m;
-        for (int d = 0; d < 3; ++d) c[d] = best[d];
-        return std::min(Rm, Rb);
+        double R = std::min(Rm, Rb), x[3];
+        for (int d = 0; d < 3; ++d) c[d] = x[d] = best[d];
+        for (int it = 1; it <= steps; ++it) {
+            int far = a;
+            double fd = -1, v[3] = {0, 0, 0};
+            for (int k = a; k < b; ++k) {
+                const double *p = r->sphere_centre + 3 * order[k];
+                const double d3[3] = {p[0] - x[0], p[1] - x[1], p[2] - x[2]};
+                const double dk = norm3(d3) + r->sphere_radius[order[k]];
+                if (dk > fd) fd = dk, far = k, v[0] = d3[0], v[1] = d3[1], v[2] = d3[2];
+            }
+            const double n = norm3(v), rad = r->sphere_radius[order[far]];
+            const double *p = r->sphere_centre + 3 * order[far];
+            for (int d = 0; d < 3; ++d) {
+                const double target = p[d] + (n > 0 ? v[d] / n * rad : 0.0);
+                x[d] += (target - x[d]) / (it + 1);
+            }
+            const double Rx = radius_about(x);
+            if (Rx < R) {
+                R = Rx;
+                for (int d = 0; d < 3; ++d) c[d] = x[d];
+            }
+        }
+        return R;
     };
     auto half_sphere = [&](int a, int b) {
         double c[3];
@@ -310,6 +334,17 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         return float4{static_cast<float>(c[0]), static_cast<float>(c[1]), static_cast<float>(c[2]),
                       static_cast<float>(R) + kCoarseEps};
     };
+    // a link of 4 or more spheres splits, along the order above, where the two
+    // halves' radii sum to the least (2 spheres at least on each side)
+    for (int l = 0; l < L; ++l) {
+        LinkC &K = rp.links[l];
+        if (K.s1 - K.s0 < 4) continue;
+        double best = HUGE_VAL, c[3];
+        for (int k = K.s0 + 2; k <= K.s1 - 2; ++k) {
+            const double sum = bound_spheres(K.s0, k, c, 32) + bound_spheres(k, K.s1, c, 32);
+            if (sum < best) best = sum, K.sm = static_cast<int16_t>(k);
+        }
+    }
     for (int l = 0; l < L; ++l) {
         LinkC &K = rp.links[l];
         if (K.sm < K.s1) {
