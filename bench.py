@@ -116,6 +116,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.mark = 0
 
     def start(self):
         try:
@@ -126,6 +127,14 @@ class ClockSampler:
             self.t.start()
         except Exception:
             self.proc = None
+
+    def wait_first(self, timeout=10.0):
+        """Block until nvidia-smi has printed its first sample (it takes a
+        moment to start), then count only the samples after it."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+        self.mark = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -142,7 +151,7 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in (self.lines[self.mark:] or self.lines):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -194,7 +203,7 @@ def oracle_rate(w, budget_s=12.0, threads=None, min_edges=64):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=vpgen.TORSO8_OBB60_CAP20, choices=list(vpgen.NAMES))
@@ -260,13 +269,15 @@ def run_reference(args):
         return 0
     w = vpgen.workload(args.workload, n_edges=args.edges)
     times = []
-    rate = None
+    states = 0.0
+    # each step a bounded sample: about a minute of CPU time in all, 0.3-2 s a step
+    per_step = min(2.0, max(0.3, 60.0 / (args.warmup + args.steps)))
     for i in range(args.warmup + args.steps):
-        r, sample, cores, dt = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / max(1, args.steps)))
+        r, sample, cores, dt = oracle_rate(w, budget_s=per_step)
         if i >= args.warmup:
             times.append(dt)
-            rate = r if rate is None else rate
-    value = float(rate)
+            states += r * dt
+    value = float(states / sum(times))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -328,6 +339,7 @@ def run_native(args):
 
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)

@@ -32,11 +32,12 @@ def _deps():
 # The files that define the edge-validation kernels (device code, tables and
 # their layouts); host-side launch code, the tuner and other kernels are not.
 KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_inst_l8.cu", "vp_inst_l9.cu",
-                "vp_inst_l15.cu", "vp_inst_l17.cu")
+                "vp_inst_l15.cu", "vp_inst_l17.cu", "vp_api.cu")
 
 
 def kernel_hash() -> str:
-    """Hash of the edge-validation kernels' sources and the public header:
+    """Hash of the edge-validation kernels' sources, the packer that builds
+    their tables (vp_api.cu) and the public header:
     counters measured on one build (profiles/traffic.json) apply to another
     with the same hash."""
     import hashlib
