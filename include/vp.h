@@ -93,10 +93,12 @@ enum {
  *   sphere_link[s], sphere_centre [S][3] (in the link's frame), sphere_radius[s].
  *   link_spheres     [D+1][4] conservative bounding sphere per link (centre in
  *                    the link frame, radius; radius <= 0 for a link with no
- *                    spheres), or NULL to derive them (centre = mean of the
- *                    link's sphere centres, radius = max |c_s - c| + r_s).
- *                    Given spheres must contain every sphere of their link
- *                    (else VP_ERR_ARG).  The paper's "mid-phase" (Sec. III-D).
+ *                    spheres), or NULL.  Given spheres must contain every
+ *                    sphere of their link (else VP_ERR_ARG).  The library
+ *                    also bounds each link's spheres itself and uses the
+ *                    smaller of the two (vp_link_bounds reports the choice);
+ *                    verdicts do not depend on it.  The paper's "mid-phase"
+ *                    (Sec. III-D).
  *   self_pairs       [P][2] sphere indices checked against each other.
  */
 typedef struct {
@@ -274,6 +276,22 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
  * vp_autotune or load.  The verdicts do not depend on it. */
 vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
 vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
+
+/* The link-level spheres the validation kernels test first (Sec. III-D: one
+ * sphere per link over-approximating it), as vp_load_robot packed them, in
+ * each link's frame (host memory; synchronous; no device work).  n_links
+ * must be the robot's joint count + 1.  Outputs, each of which may be NULL:
+ *   link_sphere  [n_links][4] centre, radius: the given sphere or the
+ *                library's bound of the link's spheres, whichever is smaller
+ *                (radius < 0: the link has no spheres);
+ *   half_sphere  [n_links][2][4] for a link of 4 or more spheres, the bounds
+ *                of its two halves, tested before its spheres (radius < 0:
+ *                the link is not split);
+ *   sphere_half  [n_spheres] 0 or 1, the half holding each of the caller's
+ *                spheres (-1: its link is not split).
+ * Radii include the 1e-5 m float margin.  VP_ERR_NOT_LOADED without a robot,
+ * VP_ERR_ARG for a wrong n_links. */
+vp_status vp_link_bounds(vp_ctx *ctx, int n_links, float *link_sphere, float *half_sphere, int32_t *sphere_half);
 
 /* Batched randomized shortcutting (Sec. III-E, "Bringing it Together": the
  * planners simplify paths by randomized shortcutting).  paths: device float

@@ -95,6 +95,11 @@ class Validator:
     def set_check_order(self, prims_first):
         vp.vp_set_check_order(self.ctx, prims_first)
 
+    def link_bounds(self):
+        """(link spheres [L, 4], half spheres [L, 2, 4], half of each sphere
+        [S]) as packed for the kernels, in each link's frame."""
+        return vp.vp_link_bounds(self.ctx, self.dof + 1, self.n_spheres)
+
     def shortcut(self, paths, lengths, draws, resolution=1.0 / 32.0, stream=None):
         """Randomized shortcutting, in place on device tensors paths
         [P, W, D] float32 and lengths [P] int32, from draws [T, P, 2]."""

@@ -790,6 +790,37 @@ extern "C" vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds) {
     return VP_OK;
 }
 
+vp_status vp_link_bounds(vp_ctx *ctx, int n_links, float *link_sphere, float *half_sphere, int32_t *sphere_half) {
+    if (!ctx) return VP_ERR_ARG;
+    if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "no robot loaded");
+    const RobotParams &rp = ctx->robot;
+    if (n_links != rp.n_links) return fail(ctx, VP_ERR_ARG, "n_links %d: the robot has %d links", n_links, rp.n_links);
+    for (int l = 0; l < rp.n_links; ++l) {
+        const LinkC &K = rp.links[l];
+        const bool any = K.s0 < K.s1, split = K.sm < K.s1;
+        if (link_sphere) {
+            const float4 b = any ? K.bs : float4{0.f, 0.f, 0.f, -1.f};
+            link_sphere[4 * l + 0] = b.x;
+            link_sphere[4 * l + 1] = b.y;
+            link_sphere[4 * l + 2] = b.z;
+            link_sphere[4 * l + 3] = b.w;
+        }
+        if (half_sphere) {
+            for (int h = 0; h < 2; ++h) {
+                const float4 b = split ? rp.halves[l][h] : float4{0.f, 0.f, 0.f, -1.f};
+                float *o = half_sphere + 8 * l + 4 * h;
+                o[0] = b.x;
+                o[1] = b.y;
+                o[2] = b.z;
+                o[3] = b.w;
+            }
+        }
+        if (sphere_half)
+            for (int i = K.s0; i < K.s1; ++i) sphere_half[rp.perm[i]] = split ? (i < K.sm ? 0 : 1) : -1;
+    }
+    return VP_OK;
+}
+
 extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int prims_first) {
     if (!ctx) return VP_ERR_ARG;
     if (prims_first != 0 && prims_first != 1) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 or 1");

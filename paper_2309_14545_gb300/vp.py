@@ -37,7 +37,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
            "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest",
-           "vp_shortcut_paths", "vp_rrt_connect", "vp_fk_codegen")
+           "vp_shortcut_paths", "vp_rrt_connect", "vp_fk_codegen", "vp_link_bounds")
 
 
 class VPError(RuntimeError):
@@ -91,6 +91,7 @@ def _load_lib():
         "vp_shortcut_paths": (U, [P, P, P, I64, C.c_int32, P, C.c_int32, F, P]),
         "vp_rrt_connect": (U, [P, P, P, I64, P, C.c_int32, F, F, C.c_int32, P, P, P, P, P, P]),
         "vp_fk_codegen": (U, [P, C.c_int, C.POINTER(C.c_double)]),
+        "vp_link_bounds": (U, [P, C.c_int, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -278,6 +279,15 @@ def vp_check_order(ctx):
     r = C.c_int(0)
     _check(ctx, lib.vp_check_order(ctx, C.byref(r)))
     return r.value
+
+
+def vp_link_bounds(ctx, n_links, n_spheres):
+    """The packed link spheres, half spheres and each sphere's half (numpy)."""
+    link = np.zeros((n_links, 4), dtype=np.float32)
+    half = np.zeros((n_links, 2, 4), dtype=np.float32)
+    which = np.zeros(n_spheres, dtype=np.int32)
+    _check(ctx, lib.vp_link_bounds(ctx, int(n_links), link.ctypes.data, half.ctypes.data, which.ctypes.data))
+    return link, half, which
 
 
 def vp_nearest(ctx, points, queries, index, dist2=None, stream=None):
