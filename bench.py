@@ -215,6 +215,8 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="pin the batched tiling (9 comma-separated lanes per edge) instead of autotuning")
     ap.add_argument("--screen", type=int, default=None, help="pin the screening rounds (with --tiling)")
+    ap.add_argument("--leg", default=None, choices=["grads", "nearest", "shortcut", "rrt", "fk"],
+                    help="run only this secondary leg and print its result (for profiling one kernel)")
     ap.add_argument("--check-order", type=int, default=None, choices=[0, 1],
                     help="pin the check order (1: primitives before self pairs); with --tiling, or in plain mode")
     return ap.parse_args()
@@ -695,10 +697,29 @@ def _traffic(args, E, mode):
         return None
 
 
+def run_leg(args):
+    """One secondary leg on its own (the same call the full run makes), so a
+    profiler sees only that leg's kernels."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    peak = 2 * 128 * props.multi_processor_count * 2070.0 * 1e6 / 1e12
+    legs = {"grads": lambda: grads_leg(dev, flush, stream), "nearest": lambda: nn_leg(dev, flush, stream, peak),
+            "shortcut": lambda: shortcut_leg(dev, flush, stream), "rrt": lambda: rrt_leg(dev, flush, stream),
+            "fk": lambda: fk_leg(dev, flush, stream)}
+    print(json.dumps({"leg": args.leg, "result": legs[args.leg]()}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_native(args)
 
 
