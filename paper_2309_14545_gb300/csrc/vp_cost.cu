@@ -4,12 +4,15 @@
 //
 // One thread per configuration.  Forward: pose the links joint by joint; for
 // each sphere accumulate the cost and g_s = dc/dc_s = sum_o -2 pen grad d;
-// per link keep G = sum g_s, M = sum c_s x g_s and the joint's world axis a
-// and origin p.  Backward: sweep the links from the leaves to the base,
-// adding each link's (G, M) into its parent's, so that for joint j
+// per link keep G = sum g_s and M = sum c_s x g_s.  Backward: sweep the links
+// from the leaves to the base, adding each link's (G, M) into its parent's,
+// so that each link holds the sums over the subtree its joint moves.  Then
+// pose again (FK is a few hundred FMAs against thousands of ball tests) to
+// get each joint's world axis a and origin p, and
 //   dc/dq_j = a_j . (M_j - p_j x G_j)   (revolute)
-//   dc/dq_j = a_j . G_j                 (prismatic)
-// with G_j, M_j summed over the subtree the joint moves.
+//   dc/dq_j = a_j . G_j                 (prismatic).
+// Keeping only (G, M) per link, not the axes and origins as well, halves the
+// shared memory a thread holds, which sets how many warps an SM keeps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,7 +24,7 @@ namespace vp {
 
 namespace {
 
-constexpr int kLinkFloats = 12;  // a, p, G, M per link and lane
+constexpr int kLinkFloats = 6;  // G, M per link and lane
 
 struct LinkStore {
     float *base;
@@ -137,7 +140,6 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
         fr_identity(f);
         float c = 0.f;
         for (int l = 0; l <= D; ++l) {
-            float3 ax = make_float3(0.f, 0.f, 0.f);
             if (l > 0) {
                 const JointC &J = P.joints[l - 1];
                 const int pm = (J.meta >> kMetaParentShift) & 0xFF;
@@ -147,10 +149,6 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
                     stash.load_frame(pm, f);
                 apply_joint(J, qi[l - 1], f);
                 if (P.links[l].slot >= 0) stash.store_frame(P.links[l].slot, f);
-                // the joint's world axis (R_after a = R_before a about its own axis)
-                ax = make_float3(fmaf(f.r0, J.ax[0], fmaf(f.r1, J.ax[1], f.r2 * J.ax[2])),
-                                 fmaf(f.r3, J.ax[0], fmaf(f.r4, J.ax[1], f.r5 * J.ax[2])),
-                                 fmaf(f.r6, J.ax[0], fmaf(f.r7, J.ax[1], f.r8 * J.ax[2])));
             }
             float3 G = make_float3(0.f, 0.f, 0.f), M = make_float3(0.f, 0.f, 0.f);
             const LinkC &L = P.links[l];
@@ -166,34 +164,45 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
                 M.y = fmaf(x.z, gs.x, fmaf(-x.x, gs.z, M.y));
                 M.z = fmaf(x.x, gs.y, fmaf(-x.y, gs.x, M.z));
             }
-            if (grad != nullptr) {
-                ls.at(l, 0) = ax.x;
-                ls.at(l, 1) = ax.y;
-                ls.at(l, 2) = ax.z;
-                ls.at(l, 3) = f.px;
-                ls.at(l, 4) = f.py;
-                ls.at(l, 5) = f.pz;
-                ls.at(l, 6) = G.x;
-                ls.at(l, 7) = G.y;
-                ls.at(l, 8) = G.z;
-                ls.at(l, 9) = M.x;
-                ls.at(l, 10) = M.y;
-                ls.at(l, 11) = M.z;
+            if (grad != nullptr && l > 0) {
+                ls.at(l, 0) = G.x;
+                ls.at(l, 1) = G.y;
+                ls.at(l, 2) = G.z;
+                ls.at(l, 3) = M.x;
+                ls.at(l, 4) = M.y;
+                ls.at(l, 5) = M.z;
             }
         }
         cost[i] = c;
         if (grad == nullptr) continue;
-        // reverse sweep: leaves to base
+        // subtree sums, leaves to base (joints are numbered parents first)
         for (int l = D; l >= 1; --l) {
+            const int plink = (P.joints[l - 1].meta >> kMetaParentLinkShift) & 0xFF;
+            if (plink >= 1)
+                for (int k = 0; k < kLinkFloats; ++k) ls.at(plink, k) += ls.at(l, k);
+        }
+        // pose again for each joint's world axis and origin
+        fr_identity(f);
+        for (int l = 1; l <= D; ++l) {
             const JointC &J = P.joints[l - 1];
-            const float Gx = ls.at(l, 6), Gy = ls.at(l, 7), Gz = ls.at(l, 8);
-            const float Mx = ls.at(l, 9), My = ls.at(l, 10), Mz = ls.at(l, 11);
-            const float ax = ls.at(l, 0), ay = ls.at(l, 1), az = ls.at(l, 2);
+            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+            if (pm == kParentBase)
+                fr_identity(f);
+            else if (pm != kParentPrev)
+                stash.load_frame(pm, f);
+            apply_joint(J, qi[l - 1], f);
+            if (P.links[l].slot >= 0) stash.store_frame(P.links[l].slot, f);
+            // the joint's world axis (R_after a = R_before a about its own axis)
+            const float ax = fmaf(f.r0, J.ax[0], fmaf(f.r1, J.ax[1], f.r2 * J.ax[2]));
+            const float ay = fmaf(f.r3, J.ax[0], fmaf(f.r4, J.ax[1], f.r5 * J.ax[2]));
+            const float az = fmaf(f.r6, J.ax[0], fmaf(f.r7, J.ax[1], f.r8 * J.ax[2]));
+            const float Gx = ls.at(l, 0), Gy = ls.at(l, 1), Gz = ls.at(l, 2);
             float gj;
             if (J.meta & kMetaPrismatic) {
                 gj = fmaf(ax, Gx, fmaf(ay, Gy, az * Gz));
             } else {
-                const float px = ls.at(l, 3), py = ls.at(l, 4), pz = ls.at(l, 5);
+                const float Mx = ls.at(l, 3), My = ls.at(l, 4), Mz = ls.at(l, 5);
+                const float px = f.px, py = f.py, pz = f.pz;
                 // M - p x G
                 const float tx = Mx - fmaf(py, Gz, -pz * Gy);
                 const float ty = My - fmaf(pz, Gx, -px * Gz);
@@ -201,16 +210,6 @@ __global__ void __launch_bounds__(128) cost_kernel(const __grid_constant__ Robot
                 gj = fmaf(ax, tx, fmaf(ay, ty, az * tz));
             }
             grad[i * D + (l - 1)] = gj;
-            // hand the subtree sums to the parent link (the base needs none)
-            const int plink = (J.meta >> kMetaParentLinkShift) & 0xFF;
-            if (plink >= 1) {
-                ls.at(plink, 6) += Gx;
-                ls.at(plink, 7) += Gy;
-                ls.at(plink, 8) += Gz;
-                ls.at(plink, 9) += Mx;
-                ls.at(plink, 10) += My;
-                ls.at(plink, 11) += Mz;
-            }
         }
     }
 }
