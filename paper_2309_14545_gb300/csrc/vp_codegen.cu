@@ -96,10 +96,12 @@ std::string fk_source(const RobotParams &P) {
     const int D = P.n_joints, S = P.n_spheres;
     std::string s;
     // one configuration per thread; rows staged in shared memory, then the
-    // block writes its configurations' rows as one contiguous stream
+    // block's rows (one contiguous range of the output) leave in a single
+    // TMA bulk store, so the warp does not spend hundreds of load/store
+    // instructions on the write-out
     s += "extern \"C\" __global__ void __launch_bounds__(32) fk_gen(const float *__restrict__ q, long long N,\n"
          "                                                         float *__restrict__ out) {\n"
-         "    extern __shared__ float buf[];\n"
+         "    extern __shared__ __align__(16) float buf[];\n"
          "    const long long base = (long long)blockIdx.x * blockDim.x;\n"
          "    const long long i = base + threadIdx.x;\n"
          "    if (i < N) {\n";
@@ -197,11 +199,24 @@ std::string fk_source(const RobotParams &P) {
         spheres_of(l);
     }
     s += "    }\n"
-         "    __syncthreads();\n"
          "    const long long rows = min((long long)blockDim.x, N - base);\n";
     s += "    const long long count = rows * " + std::to_string(3 * S) + ";\n";
-    s += "    float *dst = out + base * " + std::to_string(3 * S) + ";\n"
-         "    for (long long e = threadIdx.x; e < count; e += blockDim.x) dst[e] = buf[e];\n"
+    s += "    float *dst = out + base * " + std::to_string(3 * S) + ";\n";
+    // the bulk copy wants 16-byte aligned addresses and a multiple of 16
+    // bytes: the whole rows when the output is aligned, else nothing; the
+    // last few floats of a ragged range go by plain stores
+    s += "    const long long bulk = (reinterpret_cast<unsigned long long>(dst) & 15ull) ? 0 : ((count * 4) & ~15ll);\n"
+         "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n"
+         "    __syncthreads();\n"
+         "    if (threadIdx.x == 0 && bulk > 0) {\n"
+         "        unsigned sa;\n"
+         "        asm volatile(\"{ .reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t; }\" : \"=r\"(sa) : \"l\"(buf));\n"
+         "        asm volatile(\"cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\"\n"
+         "                     :: \"l\"(dst), \"r\"(sa), \"r\"((unsigned)bulk) : \"memory\");\n"
+         "        asm volatile(\"cp.async.bulk.commit_group;\" ::: \"memory\");\n"
+         "    }\n"
+         "    for (long long e = bulk / 4 + threadIdx.x; e < count; e += blockDim.x) dst[e] = buf[e];\n"
+         "    if (threadIdx.x == 0 && bulk > 0) asm volatile(\"cp.async.bulk.wait_group.read 0;\" ::: \"memory\");\n"
          "}\n";
     return s;
 }
