@@ -42,8 +42,9 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) states_kernel(const __grid_constan
 
 // FK sphere centres: one thread per configuration, a block of kFkConfigs
 // consecutive configurations.  The centres go to shared memory first (in the
-// caller's sphere order), then the block writes its configurations' rows as
-// one contiguous, coalesced stream.
+// caller's sphere order); the block's rows are one contiguous range of the
+// output and leave in a single TMA bulk store (cp.async.bulk), whole 16-byte
+// units of it when the output is 16-byte aligned, the rest by plain stores.
 __global__ void __launch_bounds__(32) fk_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
                                                 const long long N, float *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -84,11 +85,22 @@ __global__ void __launch_bounds__(32) fk_kernel(const __grid_constant__ RobotPar
             }
         }
     }
-    __syncthreads();
     const long long rows = min(static_cast<long long>(cpb), N - base);
     const long long count = rows * 3 * S;
     float *dst = out + base * 3 * S;
-    for (long long e = threadIdx.x; e < count; e += cpb) dst[e] = buf[e];
+    const long long bulk = (reinterpret_cast<uintptr_t>(dst) & 15u) ? 0 : ((count * 4) & ~15ll);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged rows visible to the bulk copy
+    __syncthreads();
+    if (threadIdx.x == 0 && bulk > 0) {
+        const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(buf));
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(sa),
+                     "r"(static_cast<unsigned>(bulk))
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    for (long long e = bulk / 4 + threadIdx.x; e < count; e += cpb) dst[e] = buf[e];
+    // shared memory stays allocated until the bulk copy has read it
+    if (threadIdx.x == 0 && bulk > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 __global__ void counts_kernel(const int D, const float *__restrict__ q0, const float *__restrict__ q1,

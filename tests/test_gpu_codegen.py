@@ -64,3 +64,31 @@ def test_reloading_the_robot_drops_the_generated_kernel(vpmod):
     want = oracle.Oracle(b, EMPTY_ENV).fk(q.cpu().numpy().astype(np.float64))
     assert np.abs(out.cpu().numpy() - want).max() < 1e-5
     val.close()
+
+
+def test_generated_fk_ragged_and_unaligned_output(vpmod):
+    """Both FK kernels write each block's rows with one bulk copy.  An odd
+    sphere count leaves a last block whose bytes are not a multiple of 16
+    (the remainder goes by plain stores), and an output that starts off a
+    16-byte boundary takes plain stores only: both give the same centres."""
+    Validator, vp = vpmod
+    S, N = 13, 4099
+    r = random_chain(np.random.default_rng(6), D=5, n_spheres=S)
+    val = Validator(r, EMPTY_ENV)
+    q = torch.from_numpy(vpgen.uniform_configs(r, N, seed=3)).cuda()
+    table = val.fk_spheres(q).cpu().numpy()
+    raw_t = torch.zeros(N * S * 3 + 1, dtype=torch.float32, device="cuda")
+    vp.vp_fk_spheres(val.ctx, q, raw_t[1:].view(N, S, 3))
+    assert np.array_equal(raw_t[1:].view(N, S, 3).cpu().numpy(), table) and raw_t[0].item() == 0.0
+    val.fk_codegen(True)
+    gen = val.fk_spheres(q).cpu().numpy()
+    assert np.abs(gen - table).max() <= 4e-7 * max(1.0, np.abs(table).max())
+    want = oracle.Oracle(r, EMPTY_ENV).fk(q.cpu().numpy().astype(np.float64))
+    assert np.abs(gen - want).max() < 1e-5
+    raw = torch.zeros(N * S * 3 + 1, dtype=torch.float32, device="cuda")
+    shifted = raw[1:].view(N, S, 3)
+    assert shifted.data_ptr() % 16 != 0
+    vp.vp_fk_spheres(val.ctx, q, shifted)
+    assert np.array_equal(shifted.cpu().numpy(), gen)
+    assert raw[0].item() == 0.0
+    val.close()
