@@ -79,3 +79,34 @@ def test_gradient_matches_central_differences(name):
         assert np.abs(g[i] - f1).max() <= 1e-6 * scale, (i, g[i], f1)
         checked += 1
     assert checked >= 50 and skipped <= 0.05 * (checked + skipped)
+
+
+def test_gradient_on_a_branching_tree_matches_central_differences():
+    """A tree (two branches off joint 1, a second root at joint 6) with
+    general origin rotations, general axes and prismatic joints: the oracle's
+    Jacobian loop must follow each joint's subtree, which a serial chain does
+    not exercise.  Central FD in FP64, kink samples skipped and counted."""
+    from robots_small import random_chain
+    rng = np.random.default_rng(21)
+    r = random_chain(rng, D=9, n_spheres=40)
+    r.joint_parent = np.array([-1, 0, 1, 2, 1, 4, -1, 6, 3], dtype=np.int32)
+    env = env_of(spheres=[(0.1, 0.0, 0.2, 0.3), (-0.2, 0.3, 0.1, 0.25)],
+                 capsules=[(0.0, -0.3, 0.0, 0.3, 0.2, 0.3, 0.08)],
+                 cuboids=[(0.2, 0.2, -0.1, 1, 0, 0, 0, 1, 0, 0, 0, 1, 0.15, 0.2, 0.1)])
+    o = oracle.Oracle(r, env)
+    m = 0.02
+    q = rng.uniform(-2.0, 2.0, size=(200, 9))
+    c, g = o.cost(q, m)
+    checked = skipped = 0
+    for i in range(q.shape[0]):
+        if c[i] == 0.0:
+            continue
+        f1 = _fd(o, q[i], m, 1e-6)
+        f2 = _fd(o, q[i], m, 2e-6)
+        scale = max(1.0, np.abs(f1).max())
+        if np.abs(f1 - f2).max() > 1e-6 * scale:
+            skipped += 1
+            continue
+        assert np.abs(g[i] - f1).max() <= 1e-6 * scale, (i, g[i], f1)
+        checked += 1
+    assert checked >= 50 and skipped <= 0.1 * (checked + skipped)
