@@ -65,10 +65,14 @@ def test_single_prismatic_is_translation():
         np.testing.assert_allclose(c[0], t0 + R0 @ (a * q + local), atol=1e-12)
 
 
-def test_random_chain_matches_scipy_composition():
-    """General chain: compose the frames with scipy rotations, independently."""
+@pytest.mark.parametrize("parents", [None, [-1, 0, 1, 2, 1, 4, -1, 6, 3]])
+def test_random_chain_matches_scipy_composition(parents):
+    """General chain, and a tree (two branches off joint 1, a second root at
+    joint 6): compose the frames with scipy rotations, independently."""
     rng = np.random.default_rng(3)
-    r = random_chain(rng, D=6, n_spheres=15)
+    r = random_chain(rng, D=6 if parents is None else len(parents), n_spheres=15)
+    if parents is not None:
+        r.joint_parent = np.array(parents, dtype=np.int32)
     o = oracle.Oracle(r, EMPTY_ENV)
     for _ in range(20):
         q = rng.uniform(-2, 2, size=r.dof)
