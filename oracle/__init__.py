@@ -74,7 +74,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
+            # VP_ORACLE_LIB: a prebuilt copy to load instead (the mutation
+            # test points it at a copy with a planted mistake)
+            lib = C.CDLL(os.environ.get("VP_ORACLE_LIB") or build())
             P, I64, I32, D, F = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float
             sig = {
                 "vpo_link_frames": (None, [P, P, P]),

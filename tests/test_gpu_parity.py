@@ -82,6 +82,12 @@ def test_edge_counts_bit_exact(vpmod):
     got = val.edge_counts(_cuda(q0), _cuda(q1), w.res).cpu().numpy()
     assert list(got) == [2, 33, 3, -1, -1, -1]
     assert np.array_equal(got, o.edge_count(q0, q1, w.res))
+    # the quotient is a float32 division: 0.3f / 0.1f rounds to 3.0f, so k = 4
+    # (exact division would give 5)
+    q1d = np.zeros((1, 7), np.float32)
+    q1d[0, 0] = np.float32(0.3)
+    got = val.edge_counts(_cuda(np.zeros((1, 7), np.float32)), _cuda(q1d), 0.1).cpu().numpy()
+    assert list(got) == [4]
 
 
 def _compare_states(val, o, q):

@@ -37,6 +37,18 @@ def test_edge_count_is_decided_in_float32():
     assert _count(o, [np.float32(-1e-8), 0], [1.0, 0]) == 33
 
 
+def test_edge_count_division_is_float32():
+    """The quotient is a float32 division too: 0.3f / 0.1f is exactly
+    3.0000000745... (checked with exact rationals), which float32 rounds to
+    3.0, so k = 3 + 1; exact or float64 division would give ceil = 4, k = 5."""
+    from fractions import Fraction
+    o = oracle.Oracle(planar2(), EMPTY_ENV)
+    d, r = np.float32(0.3), np.float32(0.1)
+    exact = Fraction(float(d)) / Fraction(float(r))
+    assert 3 < exact < Fraction(3) + Fraction(1, 10 ** 7)
+    assert _count(o, [0, 0], [d, 0], res=r) == 4
+
+
 def test_edge_count_non_finite():
     o = oracle.Oracle(planar2(), EMPTY_ENV)
     assert _count(o, [np.nan, 0], [0, 0]) == -1

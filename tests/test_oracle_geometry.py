@@ -141,6 +141,48 @@ def test_clearance_is_min_over_terms():
     assert o.clearance(np.array([[np.pi / 2]]))[0] == pytest.approx(0.0, abs=1e-15)
 
 
+def test_clearance_takes_each_kind_of_term():
+    """Scenes where each kind of term is the binding minimum, with the value
+    from a closed form: a self pair (both radii), a capsule beyond its end
+    cap, and a rotated cuboid above a face.  One fixed sphere of radius 0.05
+    at (0.1, 0.2, 0.3) on the base link; a moving sphere at (cos q, sin q, 0)."""
+    rob = one_joint(0, (0, 0, 1), local=(1.0, 0.0, 0.0), r=0.05)
+    base = np.array([0.1, 0.2, 0.3])
+    rob.self_pairs = np.array([[0, 1]], dtype=np.int32)
+    o = oracle.Oracle(rob, EMPTY_ENV)
+    for q in np.linspace(-3.0, 3.0, 13):
+        moving = np.array([np.cos(q), np.sin(q), 0.0])
+        want = np.linalg.norm(moving - base) - 0.05 - 0.05
+        assert o.clearance(np.array([[q]]))[0] == pytest.approx(want, abs=1e-12)
+    rob.self_pairs = np.zeros((0, 2), dtype=np.int32)
+    # capsule along z from 0.6 to 1.6 above the fixed sphere, radius 0.1: the
+    # nearest point is the end p0, 0.3 away
+    o = oracle.Oracle(rob, env_of(capsules=[(0.1, 0.2, 0.6, 0.1, 0.2, 1.6, 0.1)]))
+    assert o.clearance(np.array([[np.pi]]))[0] == pytest.approx(0.3 - 0.1 - 0.05, abs=1e-12)
+    # cuboid yawed by 30 degrees about z, its top face 0.3 below the fixed
+    # sphere's centre (the face's normal is z, so the yaw leaves the distance)
+    R = Rotation.from_euler("z", 30, degrees=True).as_matrix()
+    o = oracle.Oracle(rob, env_of(cuboids=[cuboid_row((0.1, 0.2, -0.1), R, (0.1, 0.1, 0.1))]))
+    assert o.clearance(np.array([[np.pi]]))[0] == pytest.approx(0.3 - 0.05, abs=1e-12)
+
+
+def test_exact_contact_is_valid():
+    """Contact is allowed (K = 0 is valid), decided on a scene whose
+    clearance is exactly 0 in binary floating point: a base sphere of radius
+    0.25 at z = 0.5 and an obstacle of radius 0.75 at z = 1.5."""
+    import vpgen
+    rob = one_joint(0, (0, 0, 1), local=(1.0, 0.0, 0.0), r=0.25)
+    rob.sphere_centre = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 0.5]])
+    rob.sphere_radius = np.array([0.05, 0.25])
+    o = oracle.Oracle(rob, env_of(spheres=[(0.0, 0.0, 1.5, 0.75)]))
+    q = np.array([[np.float32(np.pi / 2)]], dtype=np.float32)
+    assert o.clearance(q.astype(np.float64))[0] == 0.0
+    assert o.validate_edges(q, q, None, vpgen.RESOLUTION)[0] == 1
+    # a hair closer collides
+    o = oracle.Oracle(rob, env_of(spheres=[(0.0, 0.0, np.nextafter(1.5, 0.0), 0.75)]))
+    assert o.validate_edges(q, q, None, vpgen.RESOLUTION)[0] == 0
+
+
 def test_non_finite_state_is_invalid():
     o = oracle.Oracle(planar2(), EMPTY_ENV)
     K = o.clearance(np.array([[np.nan, 0.0], [0.0, np.inf], [0.1, 0.2]]))

@@ -1,0 +1,73 @@
+"""The oracle's pins against planted mistakes: each entry below changes one
+line of ``oracle/vp_oracle.c`` the way a plausible slip would (a sign, an
+index, a transposed operand, a dropped term, a clamp, the precision of an
+integer decision), builds that copy on its own, and runs the oracle's pin
+files against it through ``VP_ORACLE_LIB``.  Every mistake must fail some pin.
+The real source is never modified."""
+import os
+import subprocess
+import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "vp_oracle.c")
+PINS = ["test_oracle_edges.py", "test_oracle_geometry.py", "test_oracle_fk.py", "test_oracle_cost.py"]
+
+MUTATIONS = [
+ ("rodrigues sign", "(i == j ? 1.0 : 0.0) + s * K[3 * i + j]", "(i == j ? 1.0 : 0.0) - s * K[3 * i + j]"),
+ ("rodrigues 1+c", "+ (1.0 - c) * K2", "+ (1.0 + c) * K2"),
+ ("frame order parent/F", "        mat_mul(parent, F, PF);\n        mat_mul(PF, M", "        mat_mul(F, parent, PF);\n        mat_mul(PF, M"),
+ ("frame order PF/M", "        mat_mul(PF, M, T + 16 * (j + 1));", "        mat_mul(M, PF, T + 16 * (j + 1));"),
+ ("prismatic axis", "    m[3] = a[0] * d;", "    m[3] = a[1] * d;"),
+ ("sphere dist +r", "    return norm3(v) - sph[3];", "    return norm3(v) + sph[3];"),
+ ("capsule no upper clamp", "        if (t > 1.0) t = 1.0;\n    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    return", "    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    return"),
+ ("capsule sign", "    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    return norm3(v) - cap[6];", "    double v[3] = {w[0] + t * u[0], w[1] + t * u[1], w[2] + t * u[2]};\n    return norm3(v) - cap[6];"),
+ ("cuboid R transposed", "        double yi = R[0 * 3 + i] * d[0] + R[1 * 3 + i] * d[1] + R[2 * 3 + i] * d[2];", "        double yi = R[i * 3 + 0] * d[0] + R[i * 3 + 1] * d[1] + R[i * 3 + 2] * d[2];"),
+ ("cuboid inside 0", "    return sqrt(out2) + (emax < 0.0 ? emax : 0.0);", "    return sqrt(out2);"),
+ ("no self pairs", "    for (int p = 0; p < r->n_pairs; ++p) {\n        int a = r->pairs[2 * p], b = r->pairs[2 * p + 1];\n        double v[3]", "    for (int p = 0; p < 0; ++p) {\n        int a = r->pairs[2 * p], b = r->pairs[2 * p + 1];\n        double v[3]"),
+ ("pair radius one side", "        double k = norm3(v) - r->sphere_radius[a] - r->sphere_radius[b];", "        double k = norm3(v) - r->sphere_radius[a];"),
+ ("cuboid clearance +rs", "            double k = vpo_dist_cuboid(x, e->cuboids + 15 * o) - rs;", "            double k = vpo_dist_cuboid(x, e->cuboids + 15 * o) + rs;"),
+ ("no capsules", "        for (int o = 0; o < e->n_capsules; ++o) {\n            double k = vpo_dist_capsule", "        for (int o = 0; o < 0; ++o) {\n            double k = vpo_dist_capsule"),
+ ("valid strict", "    return vpo_state_clearance(r, e, q) >= 0.0;", "    return vpo_state_clearance(r, e, q) > 0.0;"),
+ ("count floor", "    float steps = ceilf(dmax / res);", "    float steps = floorf(dmax / res);"),
+ ("count no +1", "    int32_t k = (int32_t)steps + 1;", "    int32_t k = (int32_t)steps;"),
+ ("count in double", "    float steps = ceilf(dmax / res);", "    float steps = (float)ceil((double)dmax / (double)res);"),
+ ("t = i/k", "    double t = (double)i / (double)(k - 1);", "    double t = (double)i / (double)k;"),
+ ("skip last state", "    for (int32_t i = 0; i < k; ++i) {\n        vpo_edge_state(q0, q1, D, k, i, q);\n        if (!vpo_state_valid", "    for (int32_t i = 0; i < k - 1; ++i) {\n        vpo_edge_state(q0, q1, D, k, i, q);\n        if (!vpo_state_valid"),
+ ("classify band sign", "            if (K < -band) { cls = 1; break; }", "            if (K < band) { cls = 1; break; }"),
+ ("cost pen sign grad", "                    for (int i = 0; i < 3; ++i) g[i] += -2.0 * pen * gd[i];", "                    for (int i = 0; i < 3; ++i) g[i] += 2.0 * pen * gd[i];"),
+ ("cost margin dropped", "        double rs = r->sphere_radius[s] + margin;", "        double rs = r->sphere_radius[s];"),
+ ("grad cuboid world rotate transposed", "    for (int i = 0; i < 3; ++i) g[i] = R[3 * i + 0] * gb[0] + R[3 * i + 1] * gb[1] + R[3 * i + 2] * gb[2];", "    for (int i = 0; i < 3; ++i) g[i] = R[0 * 3 + i] * gb[0] + R[1 * 3 + i] * gb[1] + R[2 * 3 + i] * gb[2];"),
+ ("grad revolute cross sign", "                    dc[0] = a[1] * v[2] - a[2] * v[1];", "                    dc[0] = a[2] * v[1] - a[1] * v[2];"),
+ ("grad axis local", "            for (int i = 0; i < 3; ++i) a[i] = JF[4 * i] * ax[0] + JF[4 * i + 1] * ax[1] + JF[4 * i + 2] * ax[2];", "            for (int i = 0; i < 3; ++i) a[i] = ax[i];"),
+ ("grad origin after parent only", "            mat_mul(T + 16 * (r->parent[j] + 1), F, JF);", "            memcpy(JF, T + 16 * (r->parent[j] + 1), sizeof(JF));"),
+ ("grad capsule no clamp", "        if (t > 1.0) t = 1.0;\n    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    double n = norm3(v);", "    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    double n = norm3(v);"),
+ ("grad cuboid inside face sign", "        gb[imax] = y[imax] < 0.0 ? -1.0 : 1.0;", "        gb[imax] = 1.0;"),
+]
+
+
+def _caught(tmp, idx, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation {name!r} no longer matches the source"
+    path = os.path.join(tmp, f"m{idx}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(tmp, f"m{idx}.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-I", os.path.dirname(SRC), "-o", lib, path, "-lm"])
+    env = dict(os.environ, VP_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+                       + [os.path.join(HERE, p) for p in PINS], cwd=ROOT, env=env, capture_output=True, text=True)
+    return r.returncode == 1  # 1: some test failed (not a collection or usage error)
+
+
+def test_every_planted_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            caught = list(ex.map(lambda a: _caught(tmp, *a), [(i, *m) for i, m in enumerate(MUTATIONS)]))
+    survivors = [m[0] for m, c in zip(MUTATIONS, caught) if not c]
+    assert not survivors, f"no pin catches: {survivors}"
