@@ -1,10 +1,12 @@
-"""The oracle's pins against planted mistakes: each entry below changes one
-line of ``oracle/vp_oracle.c`` the way a plausible slip would (a sign, an
-index, a transposed operand, a dropped term, a clamp, the precision of an
-integer decision), builds that copy on its own, and runs the oracle's pin
-files against it through ``VP_ORACLE_LIB``.  Every mistake must fail some pin.
-The real source is never modified."""
+"""The oracle's pins against planted mistakes.  Each entry below changes one
+line of the oracle the way a plausible slip would (a sign, an index, a
+transposed operand, a dropped term, a clamp, a tie rule, the precision of a
+decision).  A C slip is built into its own copy of the library and loaded
+through ``VP_ORACLE_LIB``; a Python slip goes into a copy of the package that
+shadows the real one.  The oracle's pin files then run against the copy, and
+every slip must fail some pin.  The real sources are never modified."""
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -16,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "vp_oracle.c")
 PINS = ["test_oracle_edges.py", "test_oracle_geometry.py", "test_oracle_fk.py", "test_oracle_cost.py"]
+PY_PINS = {"nn": "test_oracle_nn.py", "shortcut": "test_oracle_shortcut.py", "rrt": "test_oracle_rrt.py"}
 
 MUTATIONS = [
  ("rodrigues sign", "(i == j ? 1.0 : 0.0) + s * K[3 * i + j]", "(i == j ? 1.0 : 0.0) - s * K[3 * i + j]"),
@@ -70,4 +73,53 @@ def test_every_planted_mistake_fails_a_pin():
         with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
             caught = list(ex.map(lambda a: _caught(tmp, *a), [(i, *m) for i, m in enumerate(MUTATIONS)]))
     survivors = [m[0] for m, c in zip(MUTATIONS, caught) if not c]
+    assert not survivors, f"no pin catches: {survivors}"
+
+
+PY_MUTATIONS = [
+ ("nn", "l1 distance", '        d = np.einsum("nmd,nmd->nm", diff, diff)', '        d = np.abs(diff).sum(axis=2)'),
+ ("nn", "ties to the highest index", "        i = np.argmin(d, axis=1)  # first minimum: the lowest index on ties", "        i = d.shape[1] - 1 - np.argmin(d[:, ::-1], axis=1)"),
+ ("nn", "second best not excluded", "            d[np.arange(b - a), i] = np.inf\n", ""),
+ ("shortcut", "round not floor", "    i = min(int(np.floor(np.float32(u0) * nf)), n - 1)", "    i = min(int(np.round(np.float32(u0) * nf)), n - 1)"),
+ ("shortcut", "no clamp", "    j = min(int(np.floor(np.float32(u1) * nf)), n - 1)", "    j = int(np.floor(np.float32(u1) * nf))"),
+ ("shortcut", "no swap", "    if i > j:\n        i, j = j, i\n", ""),
+ ("shortcut", "adjacent allowed", "    return (i, j) if j - i >= 2 else None", "    return (i, j) if j - i >= 1 else None"),
+ ("shortcut", "product in float64", "    i = min(int(np.floor(np.float32(u0) * nf)), n - 1)", "    i = min(int(np.floor(float(u0) * n)), n - 1)"),
+ ("shortcut", "splice off by one", "                paths[p, i + 1:i + 1 + (n - j)] = paths[p, j:n].copy()", "                paths[p, i:i + (n - j)] = paths[p, j:n].copy()"),
+ ("shortcut", "length off by one", "                lengths[p] = n - (j - i - 1)", "                lengths[p] = n - (j - i)"),
+ ("rrt", "ties to the highest index", "    i = int(np.argmin(acc))", "    i = int(n - 1 - np.argmin(acc[::-1]))"),
+ ("rrt", "reach strict", "    if dist <= F(rng):", "    if dist < F(rng):"),
+ ("rrt", "steer from q", "    return near + s * (q - near), ADVANCED", "    return q + s * (near - q), ADVANCED"),
+ ("rrt", "no duplicate check", "    if d2 == F(0):\n        return REACHED, i\n", ""),
+ ("rrt", "trees never swap", "        a = 1 - a\n    return 0", "    return 0"),
+ ("rrt", "meeting node twice", "                    path = pa[::-1] + pb[1:]           # start ... meet ... goal", "                    path = pa[::-1] + pb           # start ... meet ... goal"),
+ ("rrt", "iterations off by one", "                return 1, it + 1, np.array", "                return 1, it, np.array"),
+ ("rrt", "steer in float64", "    return near + s * (q - near), ADVANCED", "    return (near.astype(np.float64) + float(s) * (q.astype(np.float64) - near)).astype(F), ADVANCED"),
+ ("rrt", "nearest in float64", "        acc = acc + t[:, d] * t[:, d]     # product, then sum, each rounded", "        acc = (acc.astype(np.float64) + t[:, d].astype(np.float64) ** 2).astype(F)"),
+]
+
+
+def _py_caught(tmp, idx, mod, name, old, new):
+    import oracle
+    root = os.path.join(tmp, f"p{idx}")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(root, "oracle"),
+                    ignore=shutil.ignore_patterns("*.so", "*.so.*", "__pycache__"))
+    f = os.path.join(root, "oracle", mod + ".py")
+    src = open(f).read()
+    assert src.count(old) == 1, f"mutation {name!r} no longer matches oracle/{mod}.py"
+    with open(f, "w") as fh:
+        fh.write(src.replace(old, new))
+    env = dict(os.environ, VP_ORACLE_LIB=oracle.build(), PYTHONPATH=root + os.pathsep + ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        os.path.join(HERE, PY_PINS[mod])], cwd=root, env=env, capture_output=True, text=True)
+    return r.returncode == 1
+
+
+def test_every_planted_mistake_in_the_python_oracles_fails_a_pin():
+    import oracle
+    oracle.build()
+    with tempfile.TemporaryDirectory() as tmp:
+        with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            caught = list(ex.map(lambda a: _py_caught(tmp, *a), [(i, *m) for i, m in enumerate(PY_MUTATIONS)]))
+    survivors = [f"{m[0]}: {m[1]}" for m, c in zip(PY_MUTATIONS, caught) if not c]
     assert not survivors, f"no pin catches: {survivors}"

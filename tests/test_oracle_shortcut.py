@@ -14,7 +14,20 @@ def test_candidate_rule():
     assert candidate(0.0, 0.99, 10) == (0, 9)
     assert candidate(0.95, 0.05, 10) == (0, 9)       # swapped
     assert candidate(0.31, 0.42, 10) is None         # j - i = 1: nothing between
-    assert candidate(0.999999, 0.0, 5) == (0, 4)     # clamped to n - 1
+    assert candidate(0.999999, 0.0, 5) == (0, 4)
+    assert candidate(1.0, 0.0, 5) == (0, 4)          # floor(1 * 5) = 5, clamped to n - 1
+    assert candidate(0.0, 1.0, 5) == (0, 4)          # the same for the second draw
+    assert candidate(0.7, 0.0, 4) == (0, 2)          # floor(2.8), not its rounding
+
+
+def test_candidate_product_is_float32():
+    """u = 0.45454543828964233 (a float32) times 11 is exactly 4.99999982...
+    (checked with rationals), which float32 rounds to 5.0: the waypoint is
+    5, where exact or float64 arithmetic would give 4."""
+    from fractions import Fraction
+    u = np.float32(0.45454543828964233)
+    assert Fraction(float(u)) * 11 < 5 and np.float32(u) * np.float32(11) == np.float32(5)
+    assert candidate(u, 0.0, 11) == (0, 5)
 
 
 def test_empty_scene_hand_worked():
