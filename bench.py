@@ -149,9 +149,15 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
+        return self.summarise(self.lines[self.mark:] or self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the max clock and the throttle reasons seen, from
+        nvidia-smi CSV lines in FIELDS order (None when no line parses)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.lines[self.mark:] or self.lines):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
