@@ -35,16 +35,25 @@ KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h"
                 "vp_inst_l15.cu", "vp_inst_l17.cu", "vp_api.cu")
 
 
+def _code_only(text: str) -> str:
+    """The source with its comments and runs of whitespace removed, so that
+    edits to comments and layout leave the hash unchanged."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
-    """Hash of the edge-validation kernels' sources, the packer that builds
-    their tables (vp_api.cu) and the public header:
-    counters measured on one build (profiles/traffic.json) apply to another
-    with the same hash."""
+    """Hash of the code (comments and whitespace aside) of the
+    edge-validation kernels, the packer that builds their tables (vp_api.cu)
+    and the public header: counters measured on one build
+    (profiles/traffic.json) apply to another with the same hash."""
     import hashlib
     h = hashlib.sha256()
     for p in [os.path.join(CSRC, f) for f in KERNEL_FILES] + [os.path.join(HERE, "..", "include", "vp.h")]:
         h.update(os.path.basename(p).encode())
-        h.update(open(p, "rb").read())
+        h.update(_code_only(open(p, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -23,3 +23,11 @@ def test_clock_summary_median_max_and_reasons():
 def test_clock_summary_without_samples():
     assert bench.ClockSampler.summarise([]) is None
     assert bench.ClockSampler.summarise(["not, enough, fields"]) is None
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    from paper_2309_14545_gb300.build import _code_only
+    a = "int f(int x) {  // add one\n    return x + 1; /* the\n step */ }\n"
+    b = "int f(int x) { return x + 1; }"
+    assert _code_only(a) == _code_only(b)
+    assert _code_only("return x + 1;") != _code_only("return x + 2;")
