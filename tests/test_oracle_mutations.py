@@ -96,6 +96,13 @@ PY_MUTATIONS = [
  ("rrt", "iterations off by one", "                return 1, it + 1, np.array", "                return 1, it, np.array"),
  ("rrt", "steer in float64", "    return near + s * (q - near), ADVANCED", "    return (near.astype(np.float64) + float(s) * (q.astype(np.float64) - near)).astype(F), ADVANCED"),
  ("rrt", "nearest in float64", "        acc = acc + t[:, d] * t[:, d]     # product, then sum, each rounded", "        acc = (acc.astype(np.float64) + t[:, d].astype(np.float64) ** 2).astype(F)"),
+ ("rrt", "path orientation when B moved first", "                    path = pb[::-1] + pa[1:]", "                    path = pa[::-1] + pb[1:]"),
+ ("rrt", "goal validity ignored", "    if np.any(k < 0):", "    if k[0] < 0:"),
+ ("rrt", "no capacity check", "    if tree.n == tree.nodes.shape[0]:\n        return TRAPPED, -1\n", ""),
+ ("rrt", "band never flagged", "    band = [bool(np.any(np.abs(k) <= 1e-4))]", "    band = [False]"),
+ ("shortcut", "band on collisions", "            band[p] |= c == 2", "            band[p] |= c == 1"),
+ ("nn", "distance of the wrong row", "        d1[a:b] = d[np.arange(b - a), i]", "        d1[a:b] = d[0, i]"),
+ ("nn", "second best from the first row", "            d2[a:b] = d.min(axis=1)", "            d2[a:b] = d[0].min()"),
 ]
 
 

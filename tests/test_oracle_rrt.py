@@ -84,6 +84,30 @@ def test_a_sample_on_a_node_adds_nothing():
     np.testing.assert_array_equal(path[:, 0], np.array([-2.0, -1.0, 0.5, 2.0], F))
 
 
+def test_full_trees_are_trapped():
+    """Capacity 3 with the middle blocked: samples -1, 1, -1.5, 1.5 fill both
+    trees to 3 nodes (each connect is blocked at 0.5 or -0.5); samples -2.5
+    and 2.5 then find their tree full and add nothing."""
+    o = _slider(0.45)
+    samples = np.array([[-1.0], [1.0], [-1.5], [1.5], [-2.5], [2.5]], F)
+    solved, iters, path, band, sizes = rrt_connect(o, np.array([-2.0], F), np.array([2.0], F), samples,
+                                                   rng=1.5, res=1 / 32, cap=3)
+    assert solved == 0 and iters == 6 and path is None
+    assert sizes == (3, 3)
+
+
+def test_invalid_goal_and_band_endpoints():
+    o = _slider(0.45)
+    # the goal inside the obstacle: nothing is grown
+    solved, iters, path, band, sizes = rrt_connect(o, np.array([-2.0], F), np.array([0.2], F),
+                                                   np.array([[1.0]], F), rng=1.5, res=1 / 32, cap=8)
+    assert solved == -1 and iters == 0 and path is None
+    # a start 5e-5 m clear of the obstacle: inside the 1e-4 band, so flagged
+    solved, iters, path, band, sizes = rrt_connect(o, np.array([-0.55005], F), np.array([2.0], F),
+                                                   np.zeros((0, 1), F), rng=1.5, res=1 / 32, cap=8)
+    assert solved == 0 and band
+
+
 def test_empty_scene_one_iteration():
     """Start and goal within range of the first sample: EXTEND(A) reaches
     the sample, CONNECT(B) reaches it too: path start, sample, goal."""
