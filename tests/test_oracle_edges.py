@@ -122,3 +122,14 @@ def test_bad_counts_and_non_finite_edges_are_invalid():
     q1 = np.array([[1, 1], [1, 1], [1, 1], [np.inf, 0]], np.float32)
     assert list(o.validate_edges(q0, q1, np.array([5, 1, 5, 5], np.int32))) == [1, 0, 0, 0]
     assert list(o.validate_edges(q0, q1, None, RES)) == [1, 1, 0, 0]
+    # counts of 0 or below are invalid too (no state would be checked at all)
+    assert list(o.validate_edges(q0[:2], q1[:2], np.array([0, -3], np.int32))) == [0, 0]
+
+
+def test_over_long_edges_have_no_count():
+    """A count above 2^24 steps is refused (-1): 1e7 rad at 1/32 rad would be
+    3.2e8 steps.  The largest accepted edge has exactly 2^24 steps."""
+    o = oracle.Oracle(planar2(), EMPTY_ENV)
+    assert _count(o, [0, 0], [1e7, 0]) == -1
+    assert _count(o, [0, 0], [2.0 ** 24 / 32, 0]) == 2 ** 24 + 1
+    assert _count(o, [0, 0], [np.nextafter(np.float32(2.0 ** 24 / 32), np.float32(1e9)), 0]) == -1

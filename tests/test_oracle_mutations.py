@@ -50,6 +50,12 @@ MUTATIONS = [
  ("grad origin after parent only", "            mat_mul(T + 16 * (r->parent[j] + 1), F, JF);", "            memcpy(JF, T + 16 * (r->parent[j] + 1), sizeof(JF));"),
  ("grad capsule no clamp", "        if (t > 1.0) t = 1.0;\n    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    double n = norm3(v);", "    }\n    double v[3] = {w[0] - t * u[0], w[1] - t * u[1], w[2] - t * u[2]};\n    double n = norm3(v);"),
  ("grad cuboid inside face sign", "        gb[imax] = y[imax] < 0.0 ? -1.0 : 1.0;", "        gb[imax] = 1.0;"),
+ ("no max-steps check", "    if (!(steps <= (float)VPO_MAX_STEPS)) return -1;\n", ""),
+ ("no minimum of 2", "    return k < 2 ? 2 : k;", "    return k;"),
+ ("edge k<2 accepted", "    if (k < 2 || !endpoints_finite(q0, q1, D)) return 0;", "    if (!endpoints_finite(q0, q1, D)) return 0;"),
+ ("non-finite state not invalid", "    if (!all_finite(q, r->n_joints)) return -INFINITY;\n", ""),
+ ("non-finite endpoint count", "        if (!isfinite(q0[d]) || !isfinite(q1[d])) return -1;\n", ""),
+ ("edge state from q1", "    for (int d = 0; d < D; ++d) q[d] = (double)q0[d] + t * ((double)q1[d] - (double)q0[d]);", "    for (int d = 0; d < D; ++d) q[d] = (double)q1[d] + t * ((double)q0[d] - (double)q1[d]);"),
 ]
 
 
