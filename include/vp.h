@@ -74,11 +74,14 @@ enum {
 #define VP_MAX_SPHERES 256
 #define VP_MAX_PAIRS 1024
 #define VP_MAX_ENV_BYTES (160 * 1024) /* packed environment held in shared memory */
-#define VP_MAX_STEPS 16777216         /* longest edge, in resolution steps        */
+#define VP_MAX_STEPS 16777216         /* longest edge, in resolution steps; an
+                                       * explicit count may be at most
+                                       * VP_MAX_STEPS + 1 states              */
 
 /* Device status bits (OR-ed into the status word). */
 #define VP_DEVERR_COUNT 0x1u   /* an explicit count < 2                    */
-#define VP_DEVERR_LENGTH 0x2u  /* an edge longer than VP_MAX_STEPS steps   */
+#define VP_DEVERR_LENGTH 0x2u  /* an edge longer than VP_MAX_STEPS steps, or
+                                * an explicit count > VP_MAX_STEPS + 1     */
 #define VP_DEVERR_TIMEOUT 0x4u /* the persistent kernel's watchdog fired   */
 
 /*
@@ -169,11 +172,15 @@ vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float re
 
 /* Edge validity (Sec. III-D): valid[e] = 1 iff every state
  * q(t) = q0 + t (q1 - q0), t = i/(k-1), i = 0..k-1, is valid, where k is
- * counts[e] (device int32 [E], each >= 2) or, with counts == NULL, the count
- * from `resolution` as in vp_edge_counts.  States are visited in raked order
- * (a spread set of states per round), each pose is checked link by link
- * against the bounding-sphere mid-phase, then fine spheres, then self pairs,
- * and the edge stops at the first collision.  mode: VP_MODE_*.
+ * counts[e] (device int32 [E], 2 <= k <= VP_MAX_STEPS + 1) or, with
+ * counts == NULL, the count from `resolution` as in vp_edge_counts.  An
+ * explicit count below 2 sets VP_DEVERR_COUNT, one above VP_MAX_STEPS + 1
+ * sets VP_DEVERR_LENGTH; either edge is reported invalid.  States are
+ * visited in raked order (a spread set of states per round).  Each state is
+ * posed (every link), then checked in the order vp_set_check_order selects:
+ * self pairs (link-pair bounding spheres, then sphere pairs) and primitives
+ * (link bounding spheres -- the mid-phase -- then fine spheres); the edge
+ * stops at the first collision.  mode: VP_MODE_*.
  * q0, q1: device float [E][D]; valid: device uint8 [E]. */
 vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                             float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
@@ -391,16 +398,18 @@ vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits);
  * file-scope static __device__ array of 256 + VP_NOALLOC_MAX_ENV_BYTES
  * bytes, which every GPU that loads the library holds until the process
  * exits.  An environment that packs to more than VP_NOALLOC_MAX_ENV_BYTES
- * (sphere 16 B, capsule 32 B, cuboid 64 B each) is rejected with
- * VP_ERR_CAPACITY before anything runs.  The call calls no cudaMalloc,
+ * (48 B per sphere, 64 B per capsule, 96 B per cuboid: each primitive with
+ * its world box, as for vp_env_desc) is rejected with VP_ERR_CAPACITY
+ * before anything runs.  The call calls no cudaMalloc,
  * cudaFree or other device-allocating routine; host side it packs the robot
  * with small temporaries and stages the environment in a per-thread static
  * buffer.
  *
  * Runs on the calling thread's current device.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and the
- * device's launch limits; make that first call before any stream capture.
- * Every call shares the array and it keeps the previous call's contents:
+ * device's launch limits.  Every call copies the environment from pageable
+ * host memory and synchronises `stream`, so a call cannot be recorded into
+ * a CUDA graph by stream capture.  Every call shares the array and it keeps the previous call's contents:
  * each call restages the environment and clears the status word on
  * `stream` first.  Calls that overlap on the GPU (other host threads, other
  * streams) race on the array and must be serialised by the caller.

@@ -250,7 +250,7 @@ static int endpoints_finite(const float *q0, const float *q1, int32_t D)
 int vpo_edge_valid(const vpo_robot *r, const vpo_env *e, const float *q0, const float *q1, int32_t k)
 {
     int D = r->n_joints;
-    if (k < 2 || !endpoints_finite(q0, q1, D)) return 0;
+    if (k < 2 || k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) return 0;
     double q[VPO_MAX_JOINTS];
     for (int32_t i = 0; i < k; ++i) {
         vpo_edge_state(q0, q1, D, k, i, q);
@@ -267,7 +267,7 @@ int64_t vpo_validate_edges(const vpo_robot *r, const vpo_env *e, const float *q0
     for (int64_t i = 0; i < E; ++i) {
         const float *a = q0 + i * D, *b = q1 + i * D;
         int32_t k = counts ? counts[i] : vpo_edge_count(a, b, D, res);
-        if (k < 2) ++bad;
+        if (k < 2 || k > VPO_MAX_STEPS + 1) ++bad;
         valid[i] = (uint8_t)vpo_edge_valid(r, e, a, b, k);
     }
     return bad;
@@ -279,7 +279,7 @@ int vpo_edge_classify(const vpo_robot *r, const vpo_env *e, const float *q0, con
     int D = r->n_joints;
     int32_t nb = 0, ne = 0;
     int cls = 0;
-    if (k < 2 || !endpoints_finite(q0, q1, D)) {
+    if (k < 2 || k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) {
         cls = 1;
     } else {
         double q[VPO_MAX_JOINTS];

@@ -90,10 +90,13 @@ int vpo_state_valid(const vpo_robot *r, const vpo_env *e, const double *q);
 int32_t vpo_edge_count(const float *q0, const float *q1, int32_t D, float res);
 /* State i of a k-state edge, in double. */
 void vpo_edge_state(const float *q0, const float *q1, int32_t D, int32_t k, int32_t i, double *q);
-/* Edge verdict (1 = every state valid), linear order; k <= 0 means invalid. */
+/* Edge verdict (1 = every state valid), linear order.  A count below 2 or
+ * above VPO_MAX_STEPS + 1 (longer than any edge a resolution may give) makes
+ * the edge invalid without checking a state. */
 int vpo_edge_valid(const vpo_robot *r, const vpo_env *e, const float *q0, const float *q1, int32_t k);
 /* Verdicts for E edges; counts may be NULL (then k follows from res).
- * Returns the number of edges whose count was invalid (they are reported invalid). */
+ * Returns the number of edges whose count was invalid (below 2, above
+ * VPO_MAX_STEPS + 1, or none; they are reported invalid). */
 int64_t vpo_validate_edges(const vpo_robot *r, const vpo_env *e, const float *q0, const float *q1,
                            const int32_t *counts, float res, int64_t E, uint8_t *valid);
 

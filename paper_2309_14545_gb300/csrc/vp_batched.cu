@@ -52,6 +52,9 @@ __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, c
             if (k < 2) {
                 atomicOr(status, VP_DEVERR_COUNT);
                 k = -1;
+            } else if (k > VP_MAX_STEPS + 1) {
+                atomicOr(status, VP_DEVERR_LENGTH);
+                k = -1;
             }
         } else if (fin) {
             k = count_from_dmax(dmax, res);

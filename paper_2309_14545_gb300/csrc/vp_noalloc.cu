@@ -158,6 +158,10 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int bps = 0;
     e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, ev.staged != 0, smem, block, &bps);
+    if (e == cudaSuccess && bps < 1) {  // the same status the context path reports
+        set_msg(errbuf, errbuf_len, "plain edge kernel cannot be resident");
+        return VP_ERR_CAPACITY;
+    }
     // the array keeps the previous call's contents: restage the environment
     // and clear the status word on every call
     if (e == cudaSuccess && n4 > 0)
@@ -166,7 +170,7 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     if (e == cudaSuccess) {
         const int wpb = block / 32;
         const int64_t need = (n_edges + wpb - 1) / wpb;
-        const int64_t cap = static_cast<int64_t>(bps > 0 ? bps : 1) * ds->num_sms;
+        const int64_t cap = static_cast<int64_t>(bps) * ds->num_sms;
         const int grid = static_cast<int>(need < cap ? need : cap);
         e = launch_edges_plain(rp, ev, q0, q1, counts, resolution, n_edges, valid, status, nullptr, grid, block,
                                smem, s);

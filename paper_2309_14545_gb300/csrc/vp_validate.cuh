@@ -126,6 +126,9 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_co
             if (k < 2) {
                 ok = false;
                 if (lane == 0) atomicOr(status, VP_DEVERR_COUNT);
+            } else if (k > VP_MAX_STEPS + 1) {  // as long as the longest edge a resolution may give
+                ok = false;
+                if (lane == 0) atomicOr(status, VP_DEVERR_LENGTH);
             }
         } else if (ok) {
             k = count_from_dmax(dmax, res);

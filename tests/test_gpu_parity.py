@@ -180,6 +180,29 @@ def test_edge_edge_cases(vpmod):
     assert val.sync_status()[0] == vp.VP_OK  # cleared
 
 
+def test_explicit_count_bound(vpmod):
+    """An explicit count past the longest edge a resolution may give
+    (VP_MAX_STEPS + 1 states) is refused on the device in every mode: the
+    edge is invalid and the status word carries VP_DEVERR_LENGTH.  The
+    largest accepted count is checked like any other.  Constant edges at a
+    colliding configuration keep each accepted edge short to decide."""
+    from paper_2309_14545_gb300 import vp
+    w, val, o = _setup(vpmod, vpgen.ARM7_SPHERES16, 2000)
+    K = o.clearance(w.q0.astype(np.float64))
+    q_col = w.q0[np.nonzero(K < -0.01)[0][0]]
+    q = _cuda(np.repeat(q_col[None], 4, axis=0))
+    lim = vp.VP_MAX_STEPS + 1
+    counts = np.array([lim, lim + 1, 2 ** 31 - 1, 2], np.int32)
+    assert list(o.validate_edges(np.repeat(q_col[None], 4, 0), np.repeat(q_col[None], 4, 0), counts)) == [0] * 4
+    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
+        got = val.validate_edges(q, q, _cuda(counts), float(w.res), mode=mode).cpu().numpy()
+        st, bits = val.sync_status()
+        assert list(got) == [0, 0, 0, 0], mode
+        assert st == vp.VP_ERR_DEVICE and bits == vp.VP_DEVERR_LENGTH, (mode, st, bits)
+        got = val.validate_edges(q[:1], q[:1], _cuda(counts[:1]), float(w.res), mode=mode).cpu().numpy()
+        assert list(got) == [0] and val.sync_status()[0] == vp.VP_OK, mode
+
+
 def test_per_edge_launches_match_plain(vpmod):
     from paper_2309_14545_gb300 import vp
     w, val, o = _setup(vpmod, vpgen.DUAL14_SHELVES, 300)

@@ -133,3 +133,21 @@ def test_over_long_edges_have_no_count():
     assert _count(o, [0, 0], [1e7, 0]) == -1
     assert _count(o, [0, 0], [2.0 ** 24 / 32, 0]) == 2 ** 24 + 1
     assert _count(o, [0, 0], [np.nextafter(np.float32(2.0 ** 24 / 32), np.float32(1e9)), 0]) == -1
+
+
+def test_explicit_counts_past_the_step_limit_are_invalid():
+    """An explicit count may be no longer than the longest edge a resolution
+    can give (2^24 steps, 2^24 + 1 states): past that the edge is invalid
+    without a state being checked, as a count below 2 is.  In an empty scene
+    every state is valid, so only the bound can make these edges invalid;
+    the count 2^31 - 1 would otherwise take minutes of state checks."""
+    o = oracle.Oracle(planar2(), EMPTY_ENV)
+    q0 = np.zeros((1, 2), np.float32)
+    q1 = np.ones((1, 2), np.float32)
+    assert list(o.validate_edges(q0, q1, np.array([2 ** 24 + 2], np.int32))) == [0]
+    assert list(o.validate_edges(q0, q1, np.array([2 ** 31 - 1], np.int32))) == [0]
+    cls, nb = o.classify_edges(q0, q1, np.array([2 ** 24 + 2], np.int32))
+    assert list(cls) == [1] and list(nb) == [0]
+    # the longest accepted explicit count still checks its states (2^24 + 1
+    # states of a planar arm in an empty scene: a second or two)
+    assert list(o.validate_edges(q0, q1, np.array([2 ** 24 + 1], np.int32), n_threads=1)) == [1]

@@ -52,7 +52,9 @@ MUTATIONS = [
  ("grad cuboid inside face sign", "        gb[imax] = y[imax] < 0.0 ? -1.0 : 1.0;", "        gb[imax] = 1.0;"),
  ("no max-steps check", "    if (!(steps <= (float)VPO_MAX_STEPS)) return -1;\n", ""),
  ("no minimum of 2", "    return k < 2 ? 2 : k;", "    return k;"),
- ("edge k<2 accepted", "    if (k < 2 || !endpoints_finite(q0, q1, D)) return 0;", "    if (!endpoints_finite(q0, q1, D)) return 0;"),
+ ("explicit count unbounded", "    if (k < 2 || k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) return 0;", "    if (k < 2 || !endpoints_finite(q0, q1, D)) return 0;"),
+ ("classify count unbounded", "    if (k < 2 || k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) {", "    if (k < 2 || !endpoints_finite(q0, q1, D)) {"),
+ ("edge k<2 accepted", "    if (k < 2 || k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) return 0;", "    if (k > VPO_MAX_STEPS + 1 || !endpoints_finite(q0, q1, D)) return 0;"),
  ("non-finite state not invalid", "    if (!all_finite(q, r->n_joints)) return -INFINITY;\n", ""),
  ("non-finite endpoint count", "        if (!isfinite(q0[d]) || !isfinite(q1[d])) return -1;\n", ""),
  ("edge state from q1", "    for (int d = 0; d < D; ++d) q[d] = (double)q0[d] + t * ((double)q1[d] - (double)q0[d]);", "    for (int d = 0; d < D; ++d) q[d] = (double)q1[d] + t * ((double)q0[d] - (double)q1[d]);"),
