@@ -2,11 +2,14 @@
 
 A step validates one batch of synthetic edges end to end through the C ABI
 (count -> raked interpolation -> FK -> coarse/fine/self checks -> verdict).
-The default workload is the 8-DoF torso arm (100 spheres, 9 link spheres,
-200 self pairs) against 60 oriented cuboids + 20 capsules, 1,000,000 edges
-at 1/32 rad.  `value` is covered states/s (sum of the edges' state counts
-per second) with inputs resident in HBM; `e2e` is the same metric through
-pinned host buffers with the copies inside the timed region.
+The default workload is the throughput sweep: the 14-DoF dual arm (2 x 60
+spheres, 400 self pairs) against 1,000 mixed primitives (400 spheres, 300
+capsules, 300 oriented cuboids in a 2 m cube), 4,194,304 edges with state
+counts log-uniform in [2, 512].  `value` is covered states/s (sum of the
+edges' state counts per second) with inputs resident in HBM; `e2e` is the
+same metric through pinned host buffers with the copies inside the timed
+region.  The 8-DoF torso arm (1,000,000 edges at 1/32 rad) and the other
+dual-arm workloads are reported beside it under `comparisons`.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--mode plain|batched]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
@@ -106,7 +109,7 @@ def work_flops(work, robot) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    """nvidia-smi samples (every 100 ms) of SM clock and throttle reasons."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -121,7 +124,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -203,6 +206,35 @@ def oracle_rate(w, budget_s=12.0, threads=None, min_edges=64):
     return states / dt, f"first {n_full} edges of {w.name} (verdict mode, linear order, early exit)", threads, dt
 
 
+def band_subset(name, n_edges, n_sub=65536):
+    """Seeded subset of a workload's edges that the oracle classifies (the
+    same draw the GPU parity tests use)."""
+    n = min(n_sub, n_edges)
+    return np.sort(np.random.default_rng(n + vpgen.NAMES.index(name)).choice(n_edges, n, replace=False))
+
+
+def oracle_band(w, got, n_sub=65536, threads=None):
+    """Part of the CPU-baseline leg (the oracle, untimed): classify a seeded
+    subset of the workload's edges against the 1e-4 m clearance band -- an
+    edge is pinned free if every state's clearance is above it, pinned
+    colliding if some state's is below minus it, else a band edge -- count
+    the band edges and band states, and compare the GPU's verdicts `got`
+    (uint8 [E], from the timed run) on every pinned edge."""
+    import oracle
+    idx = band_subset(w.name, w.q0.shape[0], n_sub)
+    o = oracle.Oracle(w.robot, w.env)
+    t = time.perf_counter()
+    c = None if w.counts is None else w.counts[idx]
+    cls, nb = o.classify_edges(w.q0[idx], w.q1[idx], c, w.res, n_threads=threads or os.cpu_count())
+    dt = time.perf_counter() - t
+    pinned = cls != 2
+    dis = int(np.count_nonzero(got[idx][pinned] != (cls[pinned] == 0)))
+    return {"subset_edges": int(idx.size), "subset": f"seeded {idx.size}-edge subset of {w.name}",
+            "band_edges": int((cls == 2).sum()), "band_states": int(nb.sum()),
+            "pinned_free": int((cls == 0).sum()), "pinned_collide": int((cls == 1).sum()),
+            "pinned_disagreements": dis, "band_m": float(oracle.BAND), "oracle_s": dt}
+
+
 # ---------------------------------------------------------------------------
 
 
@@ -212,7 +244,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default=vpgen.TORSO8_OBB60_CAP20, choices=list(vpgen.NAMES))
+    ap.add_argument("--workload", default=vpgen.DUAL14_MIXED1000, choices=list(vpgen.NAMES))
     ap.add_argument("--edges", type=int, default=None, help="override the workload's edge count")
     ap.add_argument("--mode", default="batched", choices=["plain", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,7 +479,7 @@ def run_native(args):
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
     if not args.no_compare:
-        line["comparisons"] = compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev)
+        line["comparisons"] = compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev, peak)
         line["grads"] = grads_leg(dev, flush, stream)
         line["nearest"] = nn_leg(dev, flush, stream, peak)
         line["shortcut"] = shortcut_leg(dev, flush, stream)
@@ -458,6 +490,8 @@ def run_native(args):
         r1, sample1, _, _ = oracle_rate(w, budget_s=max(2.0, args.cpu_budget / 4), threads=1, min_edges=16)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                                 "one_thread": {"value": r1, "sample": sample1}}
+        if rank == 0:
+            line["band"] = oracle_band(w, valid.cpu().numpy())
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -481,28 +515,45 @@ def _timed(fn, flush, stream, reps):
     return float(np.median(out)), float(np.min(out))
 
 
-def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
-    """Plain single launch vs batched on the headline workload, and on the
-    dual-arm workloads (shelves: also one plain launch per edge; 1,000
-    primitives: 4,194,304 edges) and their obstacle-shifted variants.
+def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev, peak):
+    """Plain single launch vs batched on the headline workload and on the
+    others: the torso arm (1,000,000 edges at 1/32 rad), the shelves (also
+    one plain launch per edge), the 1,000-primitive scene when it is not the
+    headline, and the obstacle-shifted and mostly valid variants.  Each leg
+    carries the batched kernel's FLOP rate from its own work counters.
     Verdicts must be identical across modes."""
     import torch
     from paper_2309_14545_gb300 import Validator, vp
     res = {}
 
-    def leg(v, a, b, c, rr, n_edges, reps, per_edge=False):
+    def leg(v, wl, a, b, c, reps, per_edge=False):
+        n_edges = a.shape[0]
+        rr = float(wl.res)
         out_p = torch.empty(n_edges, dtype=torch.uint8, device=dev)
         out_b = torch.empty_like(out_p)
         v.autotune(a, b, c, rr, stream=stream)
         plain = _timed(lambda: v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_PLAIN, stream=stream, out=out_p),
                        flush, stream, reps)
-        batched = _timed(lambda: v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream, out=out_b),
-                         flush, stream, reps + 1)
+        v.kernel_time(True)
+        kms = []
+
+        def run_b():
+            v.validate_edges(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream, out=out_b)
+            kms.append(v.kernel_time(True))
+
+        batched = _timed(run_b, flush, stream, reps + 1)
+        v.kernel_time(False)
+        _, work = v.validate_edges_work(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream)
+        flops = work_flops(work.cpu().numpy(), wl.robot)
         k = c if c is not None else v.edge_counts(a, b, rr, stream=stream)
         covered = float(k.to(torch.int64).clamp(min=0).sum().item())
+        kmed = float(np.median(kms))
         d = {"edges": n_edges, "covered_states": covered,
              "plain_ms": plain[0], "batched_ms": batched[0], "batched_vs_plain": plain[0] / batched[0],
              "batched_states_per_s": covered / (batched[0] / 1e3), "plain_states_per_s": covered / (plain[0] / 1e3),
+             "batched_kernel_ms": kmed, "flops_per_step": flops,
+             "frac_of_fp32_peak": flops / (kmed / 1e3) / 1e12 / peak,
+             "tiling": v.tiling(), "screen_rounds": v.screen_rounds(), "prims_first": v.check_order(),
              "verdicts_identical": bool(torch.equal(out_p, out_b)),
              "valid_edge_fraction": float(out_b.float().mean().item())}
         if per_edge:
@@ -516,16 +567,20 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev):
         d["device_status"] = int(st)
         return d
 
-    res[w.name] = leg(val, q0, q1, counts, float(w.res), q0.shape[0], 3)
-    for name, per_edge in ((vpgen.DUAL14_SHELVES, True), (vpgen.DUAL14_MIXED1000, False),
-                           (vpgen.DUAL14_SHELVES_FAR, False), (vpgen.DUAL14_MIXED1000_FAR, False)):
+    res[w.name] = leg(val, w, q0, q1, counts, 3)
+    others = [(vpgen.TORSO8_OBB60_CAP20, False), (vpgen.DUAL14_SHELVES, True), (vpgen.DUAL14_MIXED1000, False),
+              (vpgen.DUAL14_SHELVES_FAR, False), (vpgen.DUAL14_MIXED1000_FAR, False),
+              (vpgen.DUAL14_SHELVES_MID, False), (vpgen.DUAL14_MIXED1000_MID, False)]
+    for name, per_edge in others:
+        if name == w.name:
+            continue
         wc = vpgen.workload(name)
         vc = Validator(wc.robot, wc.env, device=dev.index)
         with torch.cuda.stream(stream):
             a = torch.from_numpy(wc.q0).to(dev)
             b = torch.from_numpy(wc.q1).to(dev)
-            c = torch.from_numpy(wc.counts).to(dev)
-        res[wc.name] = leg(vc, a, b, c, float(wc.res), a.shape[0], 2, per_edge=per_edge)
+            c = None if wc.counts is None else torch.from_numpy(wc.counts).to(dev)
+        res[wc.name] = leg(vc, wc, a, b, c, 2, per_edge=per_edge)
         vc.close()
         del a, b, c
     return res

@@ -27,3 +27,22 @@ def test_every_workload_name_resolves():
     for name in vpgen.NAMES:
         w = vpgen.workload(name, n_edges=64)
         assert w.q0.shape == (64, w.robot.dof) and w.name == name
+
+
+@pytest.mark.parametrize("name,scene", [(vpgen.DUAL14_SHELVES_MID, vpgen.DUAL14_SHELVES),
+                                        (vpgen.DUAL14_MIXED1000_MID, vpgen.DUAL14_MIXED1000_FAR)])
+def test_mid_variants_draw_endpoints_near_the_middle(name, scene):
+    """The mid variants keep their scene (the shelves, or the far cube) and
+    draw both endpoints within the middle half of every joint's range, with
+    the same log-uniform counts; a prefix equals the full draw's."""
+    w = vpgen.workload(name, n_edges=70_000)
+    s = vpgen.workload(scene, n_edges=16)
+    lo, hi = w.robot.joint_lo, w.robot.joint_hi
+    mid, quarter = 0.5 * (lo + hi), 0.25 * (hi - lo)
+    for q in (w.q0, w.q1):
+        assert np.all(np.abs(q - mid) <= quarter * (1 + 1e-6))
+        assert np.all(np.abs(q - mid).max(axis=0) > 0.95 * quarter)
+    assert np.array_equal(w.env.cuboids, s.env.cuboids) and np.array_equal(w.env.spheres, s.env.spheres)
+    assert w.counts.min() >= 2 and w.counts.max() <= 512
+    p = vpgen.workload(name, n_edges=1000)
+    assert np.array_equal(p.q0, w.q0[:1000]) and np.array_equal(p.counts, w.counts[:1000])

@@ -472,6 +472,25 @@ def uniform_edges(robot: Robot, n: int, seed: int):
     return q0, q1
 
 
+def mid_edges(robot: Robot, n: int, seed: int, span: float = 0.5):
+    """Edge endpoints uniform within the middle ``span`` of each joint's
+    range, around its midpoint (configurations nearer a home pose, where a
+    two-arm robot is mostly clear of itself): (q0, q1) float32 [n, D],
+    drawn in chunks like ``uniform_edges``."""
+    D = robot.dof
+    q0 = np.empty((n, D), dtype=np.float32)
+    q1 = np.empty((n, D), dtype=np.float32)
+    lo, hi = robot.joint_lo, robot.joint_hi
+    mid, half = 0.5 * (lo + hi), 0.5 * span * (hi - lo)
+    for c0 in range(0, n, EDGE_CHUNK):
+        m = min(EDGE_CHUNK, n - c0)
+        rng = np.random.default_rng([seed, 5, c0 // EDGE_CHUNK])
+        u = rng.uniform(-1.0, 1.0, size=(2, m, D))
+        q0[c0:c0 + m] = (mid + half * u[0]).astype(np.float32)
+        q1[c0:c0 + m] = (mid + half * u[1]).astype(np.float32)
+    return q0, q1
+
+
 def loguniform_counts(n: int, seed: int, kmin: int = 2, kmax: int = 512) -> np.ndarray:
     """Explicit per-edge state counts, round(exp(U[ln kmin, ln kmax]))."""
     out = np.empty(n, dtype=np.int32)
@@ -544,7 +563,7 @@ SHORTCUT_PATHS, SHORTCUT_WAYPOINTS, SHORTCUT_ITERS, SHORTCUT_SEED = 4096, 32, 64
 
 
 # ----------------------------------------------------------------------------
-# the five workloads, by name
+# the workloads, by name
 
 ARM7_SPHERES16 = "arm7_spheres16"          # 7-DoF arm vs 16 spheres, 10,000 edges
 TORSO8_OBB60_CAP20 = "torso8_obb60_cap20"  # 8-DoF torso arm vs 60 OBBs + 20 capsules, 1,000,000 edges
@@ -558,14 +577,22 @@ DUAL14_MIXED1000 = "dual14_mixed1000"      # 14-DoF dual arm vs 1,000 mixed prim
 # obstacle placement.
 DUAL14_SHELVES_FAR = "dual14_shelves_far"      # shelves pushed 0.6 m further out
 DUAL14_MIXED1000_FAR = "dual14_mixed1000_far"  # the 2 m cube centred 1 m further out
+# Variants with mostly collision-free edges, so that the costly case -- every
+# state of a long edge checked against the whole scene -- is timed and
+# checked too: endpoints in the middle half of each joint's range (``mid``).
+# The shelves stay where they are (about 11% of these edges are valid); the
+# 1,000 primitives are those of the far variant (about 38% valid), since in
+# the base cube even these configurations almost all touch an obstacle.
+DUAL14_SHELVES_MID = "dual14_shelves_mid"
+DUAL14_MIXED1000_MID = "dual14_mixed1000_mid"
 NAMES = (ARM7_SPHERES16, TORSO8_OBB60_CAP20, DUAL14_SHELVES, ARM7_MIXED128, DUAL14_MIXED1000, DUAL14_SHELVES_FAR,
-         DUAL14_MIXED1000_FAR)
+         DUAL14_MIXED1000_FAR, DUAL14_SHELVES_MID, DUAL14_MIXED1000_MID)
 _VARIANT_OF = {DUAL14_SHELVES_FAR: DUAL14_SHELVES, DUAL14_MIXED1000_FAR: DUAL14_MIXED1000}
 
-#: Full sizes of the five workloads.
+#: Full sizes of the workloads.
 FULL_EDGES = {ARM7_SPHERES16: 10_000, TORSO8_OBB60_CAP20: 1_000_000, DUAL14_SHELVES: 262_144,
               ARM7_MIXED128: 65_536, DUAL14_MIXED1000: 4_194_304, DUAL14_SHELVES_FAR: 262_144,
-              DUAL14_MIXED1000_FAR: 4_194_304}
+              DUAL14_MIXED1000_FAR: 4_194_304, DUAL14_SHELVES_MID: 262_144, DUAL14_MIXED1000_MID: 4_194_304}
 
 DESCRIPTION = {
     ARM7_SPHERES16: "7-DoF arm (40 spheres) vs 16 spheres; 10,000 uniform edges at 1/32 rad",
@@ -578,6 +605,11 @@ DESCRIPTION = {
                       "log-uniform in [2,512]",
     DUAL14_SHELVES_FAR: "dual14_shelves with the shelf units 0.6 m further out (same edges)",
     DUAL14_MIXED1000_FAR: "dual14_mixed1000 with the 2 m cube centred 1 m further out (same edges)",
+    DUAL14_SHELVES_MID: "dual14_shelves scene; 262,144 edges between configurations in the middle half of each "
+                        "joint range, counts log-uniform in [2,512]",
+    DUAL14_MIXED1000_MID: "dual14_mixed1000_far scene (1,000 primitives, cube centred at (2, 0, 1)); 4,194,304 "
+                          "edges between configurations in the middle half of each joint range, counts "
+                          "log-uniform in [2,512]",
 }
 
 # seeds: robots 0/1/2; scenes 100 + index; edges 200 + index (index = position in NAMES)
@@ -589,7 +621,8 @@ def robot_for(name: str) -> Robot:
         return arm7(0, 40)
     if name == TORSO8_OBB60_CAP20:
         return torso_arm8(1, 100, 200)
-    if name in (DUAL14_SHELVES, DUAL14_MIXED1000, DUAL14_SHELVES_FAR, DUAL14_MIXED1000_FAR):
+    if name in (DUAL14_SHELVES, DUAL14_MIXED1000, DUAL14_SHELVES_FAR, DUAL14_MIXED1000_FAR, DUAL14_SHELVES_MID,
+                DUAL14_MIXED1000_MID):
         return dual_arm14(60, 400)
     raise ValueError(name)
 
@@ -598,7 +631,8 @@ def env_for(name: str) -> Env:
     return {ARM7_SPHERES16: env_spheres16, TORSO8_OBB60_CAP20: env_boxes_capsules, DUAL14_SHELVES: env_shelves,
             ARM7_MIXED128: env_mixed128, DUAL14_MIXED1000: env_mixed1000,
             DUAL14_SHELVES_FAR: lambda: env_shelves(push=0.6),
-            DUAL14_MIXED1000_FAR: lambda: env_mixed1000(shift=1.0)}[name]()
+            DUAL14_MIXED1000_FAR: lambda: env_mixed1000(shift=1.0), DUAL14_SHELVES_MID: env_shelves,
+            DUAL14_MIXED1000_MID: lambda: env_mixed1000(shift=1.0)}[name]()
 
 
 def workload(name: str, n_edges: Optional[int] = None, robot: Optional[Robot] = None,
@@ -622,6 +656,9 @@ def workload(name: str, n_edges: Optional[int] = None, robot: Optional[Robot] = 
         return Workload(name, robot, env, q0, q1, None, RESOLUTION)
     if name in (DUAL14_SHELVES, DUAL14_MIXED1000):
         q0, q1 = uniform_edges(robot, n, seed)
+        return Workload(name, robot, env, q0, q1, loguniform_counts(n, seed), RESOLUTION)
+    if name in (DUAL14_SHELVES_MID, DUAL14_MIXED1000_MID):
+        q0, q1 = mid_edges(robot, n, seed)
         return Workload(name, robot, env, q0, q1, loguniform_counts(n, seed), RESOLUTION)
     q = uniform_configs(robot, n, seed)
     return Workload(name, robot, env, q, q.copy(), None, RESOLUTION, margin=0.02)
