@@ -255,8 +255,9 @@ def parse():
     ap.add_argument("--screen", type=int, default=None, help="pin the screening rounds (with --tiling)")
     ap.add_argument("--leg", default=None, choices=["grads", "nearest", "shortcut", "rrt", "fk"],
                     help="run only this secondary leg and print its result (for profiling one kernel)")
-    ap.add_argument("--check-order", type=int, default=None, choices=[0, 1],
-                    help="pin the check order (1: primitives before self pairs); with --tiling, or in plain mode")
+    ap.add_argument("--check-order", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="pin the check order (bit 1: primitives before self pairs; bit 2: checks interleaved "
+                         "with posing); with --tiling, or in plain mode")
     return ap.parse_args()
 
 
@@ -474,7 +475,7 @@ def run_native(args):
                   "lane_efficiency": lane_efficiency(work),
                   "tiling": val.tiling() if mode == vp.VP_MODE_BATCHED else None,
                   "screen_rounds": val.screen_rounds() if mode == vp.VP_MODE_BATCHED else None,
-                  "prims_first": val.check_order(),
+                  "check_order": val.check_order(),
                   "tiling_source": ("pinned" if args.tiling else "autotuned") if mode == vp.VP_MODE_BATCHED else None,
                   "ms_min": float(np.min(ms)), "ms_median": float(np.median(ms)), "git": _git_rev()},
     }
@@ -543,8 +544,10 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev, peak):
 
         batched = _timed(run_b, flush, stream, reps + 1)
         v.kernel_time(False)
-        _, work = v.validate_edges_work(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream)
-        flops = work_flops(work.cpu().numpy(), wl.robot)
+        with torch.cuda.stream(stream):  # the counters are zeroed on the stream the kernel runs on
+            _, work = v.validate_edges_work(a, b, c, rr, mode=vp.VP_MODE_BATCHED, stream=stream)
+            work = work.cpu().numpy()
+        flops = work_flops(work, wl.robot)
         k = c if c is not None else v.edge_counts(a, b, rr, stream=stream)
         covered = float(k.to(torch.int64).clamp(min=0).sum().item())
         kmed = float(np.median(kms))
@@ -553,7 +556,7 @@ def compare_modes(val, w, q0, q1, counts, valid, flush, stream, dev, peak):
              "batched_states_per_s": covered / (batched[0] / 1e3), "plain_states_per_s": covered / (plain[0] / 1e3),
              "batched_kernel_ms": kmed, "flops_per_step": flops,
              "frac_of_fp32_peak": flops / (kmed / 1e3) / 1e12 / peak,
-             "tiling": v.tiling(), "screen_rounds": v.screen_rounds(), "prims_first": v.check_order(),
+             "tiling": v.tiling(), "screen_rounds": v.screen_rounds(), "check_order": v.check_order(),
              "verdicts_identical": bool(torch.equal(out_p, out_b)),
              "valid_edge_fraction": float(out_b.float().mean().item())}
         if per_edge:

@@ -177,10 +177,11 @@ vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float re
  * explicit count below 2 sets VP_DEVERR_COUNT, one above VP_MAX_STEPS + 1
  * sets VP_DEVERR_LENGTH; either edge is reported invalid.  States are
  * visited in raked order (a spread set of states per round).  Each state is
- * posed (every link), then checked in the order vp_set_check_order selects:
- * self pairs (link-pair bounding spheres, then sphere pairs) and primitives
- * (link bounding spheres -- the mid-phase -- then fine spheres); the edge
- * stops at the first collision.  mode: VP_MODE_*.
+ * posed and checked in the order vp_set_check_order selects -- every link
+ * posed first, or each link checked as soon as it is posed -- against self
+ * pairs (link-pair bounding spheres, then sphere pairs) and primitives (link
+ * bounding spheres -- the mid-phase -- then fine spheres); the edge stops at
+ * the first collision.  mode: VP_MODE_*.
  * q0, q1: device float [E][D]; valid: device uint8 [E]. */
 vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                             float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
@@ -275,14 +276,24 @@ vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n);
 vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds);
 vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 
-/* Check order of the validation kernels (edges and states, every mode):
- * after posing, self pairs then primitives (prims_first = 0, the default),
- * or primitives then self pairs (1).  Which finds a colliding configuration
- * with less work depends on the robot and scene; vp_autotune times both.
- * vp_set_check_order pins it (VP_ERR_ARG unless 0 or 1) until the next
- * vp_autotune or load.  The verdicts do not depend on it. */
-vp_status vp_set_check_order(vp_ctx *ctx, int prims_first);
-vp_status vp_check_order(vp_ctx *ctx, int *prims_first);
+/* Check order of the validation kernels (edges and states, every mode), a
+ * combination of two bits:
+ *   VP_ORDER_PRIMS_FIRST: primitives (link bounding spheres, then fine
+ *     spheres) before self pairs; without it, self pairs first;
+ *   VP_ORDER_INTERLEAVE: checks interleaved with posing, the paper's order
+ *     (Sec. III-D): links are posed in order and each is checked as soon as
+ *     it is posed (its self pairs with earlier links, and its spheres against
+ *     the primitives), so that links after a collision are never posed;
+ *     without it, every link is posed first and the checks run after.
+ * 0 (the default) is "pose all, self pairs first".  Which order finds a
+ * colliding configuration with the least work depends on the robot and the
+ * scene; vp_autotune times all four.  vp_set_check_order pins one
+ * (VP_ERR_ARG outside 0..3) until the next vp_autotune or load.  The
+ * verdicts do not depend on it. */
+#define VP_ORDER_PRIMS_FIRST 0x1
+#define VP_ORDER_INTERLEAVE 0x2
+vp_status vp_set_check_order(vp_ctx *ctx, int order);
+vp_status vp_check_order(vp_ctx *ctx, int *order);
 
 /* The link-level spheres the validation kernels test first (Sec. III-D: one
  * sphere per link over-approximating it), as vp_load_robot packed them, in

@@ -89,11 +89,13 @@ class Validator:
         vp.vp_set_screen_rounds(self.ctx, rounds)
 
     def check_order(self):
-        """1 if primitives are checked before self pairs, else 0."""
+        """The check order (VP_ORDER_* bits): 1 if primitives are checked
+        before self pairs, plus 2 if each link is checked as soon as it is
+        posed (else every link is posed first)."""
         return vp.vp_check_order(self.ctx)
 
-    def set_check_order(self, prims_first):
-        vp.vp_set_check_order(self.ctx, prims_first)
+    def set_check_order(self, order):
+        vp.vp_set_check_order(self.ctx, order)
 
     def link_bounds(self):
         """(link spheres [L, 4], half spheres [L, 2, 4], half of each sphere

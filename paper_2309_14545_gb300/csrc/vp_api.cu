@@ -589,7 +589,7 @@ extern "C" vp_status vp_validate_states(vp_ctx *ctx, const float *q, int64_t n, 
             ctx, [lmax](size_t sm, int b, bool, int *o) { return prepare_states(lmax, sm, b, o); }, &view, &block, &smem,
             &bps, &e))
         return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
-    view.prims_first = batched_check_order(ctx->batched);
+    view.order = batched_check_order(ctx->batched);
     if (e == cudaSuccess) {
         const int64_t need = (n + block - 1) / block;
         const int64_t grid =
@@ -659,7 +659,7 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
         return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges (prepare)");
     if (bps < 1) return fail(ctx, VP_ERR_CAPACITY, "plain edge kernel cannot be resident");
-    view.prims_first = batched_check_order(ctx->batched);
+    view.order = batched_check_order(ctx->batched);
     const int wpb = block / 32;
     if (mode == VP_MODE_PER_EDGE && !work) {
         const int D = ctx->robot.n_joints;
@@ -821,16 +821,16 @@ vp_status vp_link_bounds(vp_ctx *ctx, int n_links, float *link_sphere, float *ha
     return VP_OK;
 }
 
-extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int prims_first) {
+extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int order) {
     if (!ctx) return VP_ERR_ARG;
-    if (prims_first != 0 && prims_first != 1) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 or 1");
-    batched_set_check_order(ctx->batched, prims_first);
+    if (order < 0 || order >= kOrderCount) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 to 3");
+    batched_set_check_order(ctx->batched, order);
     return VP_OK;
 }
 
-extern "C" vp_status vp_check_order(vp_ctx *ctx, int *prims_first) {
-    if (!ctx || !prims_first) return VP_ERR_ARG;
-    *prims_first = batched_check_order(ctx->batched);
+extern "C" vp_status vp_check_order(vp_ctx *ctx, int *order) {
+    if (!ctx || !order) return VP_ERR_ARG;
+    *order = batched_check_order(ctx->batched);
     return VP_OK;
 }
 
@@ -913,7 +913,7 @@ extern "C" vp_status vp_rrt_connect(vp_ctx *ctx, const float *start, const float
     RRTLaunch L{start, goal, samples, B, T, cap, range, resolution, ctx->rrt_nodes, ctx->rrt_parent, ctx->rrt_queue,
                 status, iters, path, path_len, tree_sizes, ctx->batched.watchdog_ns};
     EnvView view = ctx->env;
-    view.prims_first = batched_check_order(ctx->batched);
+    view.order = batched_check_order(ctx->batched);
     std::string msg;
     const int rc = rrt_launch(ctx->robot, view, L, ctx->status, ctx->num_sms, ctx->smem_optin, st, &msg);
     if (rc == 0) return VP_OK;

@@ -139,7 +139,7 @@ struct Impl {
     float k_res = 0.f;
     int G[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     int screen_rounds = kDefaultScreenRounds;
-    int prims_first = 0;  // check order
+    int order = 0;  // check order (kOrder* bits)
     bool tuned = false;
 };
 
@@ -284,7 +284,7 @@ int batched_validate(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     EnvView view;
     rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
-    view.prims_first = im->prims_first;
+    view.order = im->order;
     const bool same = im->exec && im->k_q0 == a.q0 && im->k_q1 == a.q1 && im->k_counts == a.counts &&
                       im->k_valid == a.valid && im->k_E == a.E && im->k_res == a.res && im->k_ev == a.ev_start &&
                       im->k_watchdog == st.watchdog_ns;
@@ -328,7 +328,7 @@ int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *wor
     EnvView view;
     rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
-    view.prims_first = im->prims_first;
+    view.order = im->order;
     const cudaError_t e = enqueue(im, a, view, plan_from(im, st.watchdog_ns), smem, grid, a.stream, a.valid, work);
     return e == cudaSuccess ? 0 : set_err(msg, "batched work", e);
 }
@@ -350,7 +350,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     EnvView view;
     int rc = prepare_kernel(a, &view, &smem, &grid, msg);
     if (rc) return rc;
-    view.prims_first = im->prims_first;
+    view.order = im->order;
     const int64_t S = std::min<int64_t>(a.E, int64_t{1} << 23);
     rc = ensure_capacity(im, S, msg);
     if (rc) return rc;
@@ -389,7 +389,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         if (it != g_tune_cache.end()) {
             for (int b = 0; b < kNB; ++b) im->G[b] = it->second[b];
             im->screen_rounds = it->second[kNB];
-            im->prims_first = it->second[kNB + 1];
+            im->order = it->second[kNB + 1];
             im->tuned = true;
             drop_graph(im);
             cudaFree(tv);
@@ -411,7 +411,7 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) p.G[b] = defaults[b];
     p.screen_rounds = kDefaultScreenRounds;
-    view.prims_first = 0;
+    view.order = 0;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -463,16 +463,24 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
         p.screen_rounds = best_r;
         cur = best;
     };
-    // check order (self pairs or primitives first), the other choices held
+    // check order (self pairs or primitives first; every link posed first,
+    // or checks interleaved with posing), the other choices held
     auto tune_order = [&]() {
-        const int keep = view.prims_first;
-        view.prims_first = 1 - keep;
-        float ms = 0.f;
-        time_plan(&ms);
-        if (e == cudaSuccess && ms < 0.99f * cur)
-            cur = ms;
-        else
-            view.prims_first = keep;
+        const int keep = view.order;
+        int best_o = keep;
+        float best = cur;
+        for (int o = 0; o < kOrderCount && e == cudaSuccess; ++o) {
+            if (o == keep) continue;
+            view.order = o;
+            float ms = 0.f;
+            time_plan(&ms);
+            if (e == cudaSuccess && ms < 0.99f * best) {
+                best = ms;
+                best_o = o;
+            }
+        }
+        view.order = best_o;
+        cur = best;
     };
     tune_order();
     tune_screen();
@@ -509,14 +517,14 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     if (e != cudaSuccess) return set_err(msg, "tuning runs", e);
     for (int b = 0; b < kNB; ++b) im->G[b] = p.G[b];
     im->screen_rounds = p.screen_rounds;
-    im->prims_first = view.prims_first;
+    im->order = view.order;
     im->tuned = true;
     drop_graph(im);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         std::vector<int> v(im->G, im->G + kNB);
         v.push_back(im->screen_rounds);
-        v.push_back(im->prims_first);
+        v.push_back(im->order);
         g_tune_cache[key] = v;
     }
     return 0;
@@ -530,7 +538,7 @@ void batched_invalidate(BatchedState &st) {
     const int defaults[kNB] = {4, 8, 16, 32, 32, 32, 32, 32, 32};
     for (int b = 0; b < kNB; ++b) im->G[b] = defaults[b];
     im->screen_rounds = kDefaultScreenRounds;
-    im->prims_first = 0;
+    im->order = 0;
 }
 
 void batched_release(BatchedState &st) {
@@ -558,16 +566,16 @@ int batched_screen_rounds(const BatchedState &st) {
     return im ? im->screen_rounds : kDefaultScreenRounds;
 }
 
-void batched_set_check_order(BatchedState &st, int prims_first) {
+void batched_set_check_order(BatchedState &st, int order) {
     Impl *im = impl_of(st);
-    im->prims_first = prims_first;
+    im->order = order;
     im->tuned = true;
     drop_graph(im);
 }
 
 int batched_check_order(const BatchedState &st) {
     const Impl *im = static_cast<const Impl *>(st.impl);
-    return im ? im->prims_first : 0;
+    return im ? im->order : 0;
 }
 
 void batched_set_tiling(BatchedState &st, const int *G, int n) {

@@ -88,9 +88,9 @@ void batched_release(BatchedState &st);
 int batched_tiling(const BatchedState &st, int *G, int n);
 // Replace the first n buckets' lanes per edge (values already checked).
 void batched_set_tiling(BatchedState &st, const int *G, int n);
-// Check order of every validation kernel (1: primitives before self pairs),
-// tuned along with the tiling.
-void batched_set_check_order(BatchedState &st, int prims_first);
+// Check order of every validation kernel (kOrder* bits: primitives before
+// self pairs, checks interleaved with posing), tuned along with the tiling.
+void batched_set_check_order(BatchedState &st, int order);
 int batched_check_order(const BatchedState &st);
 // Screening rounds of the first phase (0: no limit, no second phase).
 void batched_set_screen_rounds(BatchedState &st, int rounds);

@@ -351,7 +351,7 @@ struct EnvSm {
     const float4 *bb_sph, *bb_cap, *bb_box;  // world boxes [2 n] of each kind
     int ns, nc, nb;
     int kind_order;     // kinds in visiting order, 4 bits each
-    int prims_first;    // 1: primitives before self pairs
+    int order;          // check order (kOrder* bits)
 };
 
 // Views of the environment: the block's shared copy (STAGED), or the device
@@ -370,7 +370,7 @@ __device__ __forceinline__ EnvSm env_views(const float4 *sm, const EnvView &env)
     e.nc = env.nc;
     e.nb = env.nb;
     e.kind_order = env.kind_order;
-    e.prims_first = env.prims_first;
+    e.order = env.order;
     return e;
 }
 
@@ -576,6 +576,162 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
     return false;
 }
 
+// Checks interleaved with posing: one link's primitives of one kind.  Every
+// lane's link bounding sphere (centre cl, the link's radius) is tested
+// against each primitive whose world box overlaps the link's warp-wide box
+// `lb` (lane t compares primitive k0 + t of each batch of 32), then the
+// link's fine spheres -- in the link frame f, which the posing pass holds in
+// registers -- wherever some lane's coarse test hit.  Returns the warp's
+// stop decision.
+template <int KIND, int MODE, bool STATS>
+__device__ __forceinline__ bool link_prim_pass(const RobotParams &P, int l, const Fr &f, float3 cl,
+                                               const float4 *prims, const float4 *boxes, int n, const LinkBox &lb,
+                                               Ctl &ctl, bool &col, const WorkRef<STATS> &w) {
+    using K = Kind<KIND>;
+    const int lane = threadIdx.x & 31;
+    const LinkC &L = P.links[l];
+    const float rl = L.bs.w;
+#pragma unroll 1
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int kb = k0 + lane;
+        bool ov = false;
+        if (kb < n) {
+            const float4 lo = boxes[2 * kb], hi = boxes[2 * kb + 1];
+            ov = (lo.x <= lb.hx) & (hi.x >= lb.lx) & (lo.y <= lb.hy) & (hi.y >= lb.ly) & (lo.z <= lb.hz) &
+                 (hi.z >= lb.lz);
+            w.slot(VP_WORK_BOX_TESTS, 1);
+        }
+        unsigned m = __ballot_sync(kFull, ov);
+        while (m) {  // warp-uniform: primitives whose box overlaps the link's
+            const int k = k0 + __ffs(m) - 1;
+            m &= m - 1;
+            float4 o[K::kWords];
+#pragma unroll
+            for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
+            const bool h = !ctl.idle && K::hit(cl, rl, o);
+            w.slot(VP_WORK_LANE_COARSE, 1);
+            if (!ctl.idle) w.add(K::kCoarse, 1);
+            if (!__any_sync(kFull, h)) continue;
+            float4 ol[K::kWords];
+            K::to_frame(f, o, ol);
+            int a0 = L.s0, a1 = L.s1;
+            bool hA = h, hB = h;
+            if (L.sm < L.s1) {
+                const float4 g0 = P.halves[l][0], g1 = P.halves[l][1];
+                hA = h && K::hit(make_float3(g0.x, g0.y, g0.z), g0.w, ol);
+                hB = h && K::hit(make_float3(g1.x, g1.y, g1.z), g1.w, ol);
+                w.slot(VP_WORK_LANE_COARSE, 2);
+                if (!ctl.idle) w.add(K::kCoarse, 2);
+                if (!__any_sync(kFull, hA)) a0 = L.sm;
+                if (!__any_sync(kFull, hB)) a1 = L.sm;
+            }
+            w.slot(VP_WORK_LANE_FINE, a1 - a0);
+            if (!ctl.idle) w.add(K::kFine, a1 - a0);
+            if (STATS) w.add(VP_WORK_FINE_OWN, (hA ? max(0, L.sm - a0) : 0) + (hB ? max(0, a1 - L.sm) : 0));
+#pragma unroll 1
+            for (int s = a0; s < a1; ++s) {
+                const float4 sp = P.spheres[s];
+                col |= (s < L.sm ? hA : hB) && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
+            }
+            if (group_stop<MODE>(ctl, col)) return true;
+        }
+    }
+    return false;
+}
+
+// The paper's order (Sec. III-D, checks interleaved with FK): links are
+// posed in order and each is checked as soon as it is posed -- its self
+// pairs with the links posed before it, and its bounding sphere and fine
+// spheres against the primitives -- so that once the state has collided
+// (under MODE's stop rule) no later link is posed.  Which of the link's two
+// checks comes first follows kOrderPrimsFirst.  Verdicts equal those of
+// pose_and_check's pose-all order.
+template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+__device__ __forceinline__ bool pose_and_check_interleaved(const RobotParams &P, const QF &qf, const EnvSm &env,
+                                                           const Stash &stash, const Ctl &ctl_in,
+                                                           const WorkRef<STATS> &w) {
+    bool col = false;
+    Ctl ctl = ctl_in;
+    const int D = P.n_joints;
+    const bool prims_first = (env.order & kOrderPrimsFirst) != 0;
+    const float inf = __int_as_float(0x7f800000);
+    w.add(VP_WORK_STATES, 1);
+    w.slot(VP_WORK_LANE_STATES, 1);
+    Fr f;
+    fr_identity(f);
+    FrameCursor cur_a;
+#pragma unroll 1
+    for (int l = 0; l <= D; ++l) {
+        if (l > 0) {
+            const JointC &J = P.joints[l - 1];
+            const int pm = (J.meta >> kMetaParentShift) & 0xFF;
+            if (pm == kParentBase)
+                fr_identity(f);
+            else if (pm != kParentPrev)
+                recompute_frame_cached<SIMPLE>(P, (J.meta >> kMetaParentLinkShift) & 0xFF, stash, f);
+            float ms, mc;
+            joint_motion(J, qf(l - 1), ms, mc);
+            stash.mo(l - 1, 0) = ms;
+            stash.mo(l - 1, 1) = mc;
+            apply_joint_sc<SIMPLE>(J, ms, mc, f);
+        }
+        const LinkC &L = P.links[l];
+        if (L.s0 >= L.s1) continue;  // no spheres: nothing to check on this link
+        const float3 cl = fr_apply(f, L.bs.x, L.bs.y, L.bs.z);
+        stash.store_centre(l, cl);
+        w.add(VP_WORK_LINK_CENTRES, 1);
+#pragma unroll 1
+        for (int phase = 0; phase < 2; ++phase) {
+            if ((phase == 0) != prims_first) {  // self pairs whose later link is l
+#pragma unroll 1
+                for (int g = L.g0; g < L.g1; ++g) {
+                    const GroupC G = P.groups[g];
+                    const float3 ca = stash.centre(G.la);
+                    const float dx = ca.x - cl.x, dy = ca.y - cl.y, dz = ca.z - cl.z;
+                    const float rr = P.links[G.la].bs.w + L.bs.w;
+                    const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+                    if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
+                    if (!__any_sync(kFull, wants(ctl, h))) continue;
+                    const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
+                    w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
+                    if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+                    if (!ctl.idle && h) w.add(VP_WORK_PAIR_FINE_OWN, G.p1 - G.p0);
+#pragma unroll 1
+                    for (int p = G.p0; p < G.p1; ++p) {
+                        const PairC pr = P.pairs[p];
+                        const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
+                        const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
+                        const float3 b = fr_apply(f, sb.x, sb.y, sb.z);
+                        const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+                        const float r2 = sa.w + sb.w;
+                        col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+                    }
+                    if (group_stop<MODE>(ctl, col)) return col;
+                }
+            } else {  // primitives against link l
+                const bool live = !ctl.idle;
+                const float r = L.bs.w;
+                const LinkBox lb{warp_min(live ? cl.x - r : inf), warp_min(live ? cl.y - r : inf),
+                                 warp_min(live ? cl.z - r : inf), warp_max(live ? cl.x + r : -inf),
+                                 warp_max(live ? cl.y + r : -inf), warp_max(live ? cl.z + r : -inf)};
+#pragma unroll 1
+                for (int ki = 0; ki < 3; ++ki) {
+                    const int kind = (env.kind_order >> (4 * ki)) & 15;
+                    bool stop;
+                    if (kind == 0)
+                        stop = link_prim_pass<0, MODE, STATS>(P, l, f, cl, env.sph, env.bb_sph, env.ns, lb, ctl, col, w);
+                    else if (kind == 1)
+                        stop = link_prim_pass<1, MODE, STATS>(P, l, f, cl, env.cap, env.bb_cap, env.nc, lb, ctl, col, w);
+                    else
+                        stop = link_prim_pass<2, MODE, STATS>(P, l, f, cl, env.box, env.bb_box, env.nb, lb, ctl, col, w);
+                    if (stop) return col;
+                }
+            }
+        }
+    }
+    return col;
+}
+
 // Pose one configuration and check it (Sec. III-B/C/D):
 //   1. pose every link (FK is cheap next to the checks), keeping each
 //      joint's (sin, cos) and the world centre of each link's bounding
@@ -585,7 +741,8 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 //   3. primitives, kind by kind, each against every link's bounding sphere
 //      (pairs first culled by warp-wide boxes, see prim_pass), then fine
 //      spheres where a coarse test hit.
-// Steps 2 and 3 swap when the environment view says so (prims_first).
+// Steps 2 and 3 swap when the environment view says so (kOrderPrimsFirst);
+// with kOrderInterleave the state goes to pose_and_check_interleaved.
 // Frames needed by fine tests are recomputed from the kept (sin, cos).  The
 // order of checks is chosen for early exit: a colliding configuration is
 // most often found by a self pair or a large primitive; it does not change
@@ -595,6 +752,8 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
 template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
 __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
                                                const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w) {
+    if (env.order & kOrderInterleave)
+        return pose_and_check_interleaved<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl_in, w);
     bool col = false;
     Ctl ctl = ctl_in;
     const int D = P.n_joints;
@@ -634,7 +793,7 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
     //    link boxes.
 #pragma unroll 1
     for (int phase = 0; phase < 2; ++phase) {
-        if ((phase == 0) != (env.prims_first != 0)) {  // self pairs
+        if ((phase == 0) != ((env.order & kOrderPrimsFirst) != 0)) {  // self pairs
             FrameCursor cur_a, cur_b;
             for (int g = 0; g < P.n_groups; ++g) {
                 const GroupC G = P.groups[g];

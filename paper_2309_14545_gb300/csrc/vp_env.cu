@@ -173,7 +173,7 @@ int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view
     view->n_float4 = static_cast<int>(n4);
     view->kind_order = kinds[0] | (kinds[1] << 4) | (kinds[2] << 8);
     view->staged = 1;
-    view->prims_first = 0;
+    view->order = 0;
     return 0;
 }
 

@@ -94,8 +94,16 @@ struct EnvView {
     int n_float4;    // total float4 count
     int kind_order;  // visiting order of the kinds
     int staged;      // 1: each block copies it into shared memory; 0: read in place (through L1)
-    int prims_first; // check order: 1 = primitives before self pairs (set per launch)
+    int order;       // check order (kOrder* bits, set per launch)
 };
+
+// Check order bits (EnvView::order): primitives before self pairs, and
+// checks interleaved with posing (each link checked as soon as it is posed,
+// later links left unposed once the state has collided) instead of every
+// link posed first.
+constexpr int kOrderPrimsFirst = VP_ORDER_PRIMS_FIRST;
+constexpr int kOrderInterleave = VP_ORDER_INTERLEAVE;
+constexpr int kOrderCount = 4;
 
 // Dynamic shared memory the environment takes in a block.
 __host__ __device__ inline size_t env_smem_bytes(const EnvView &env) {

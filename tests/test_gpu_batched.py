@@ -145,21 +145,28 @@ def test_second_phase_matches_plain(vpmod, name, n):
             out = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
             val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
             assert np.array_equal(out.cpu().numpy(), want), (rounds, lanes)
-    # the other check order: the same verdicts in both modes, and for states
+    # the other check orders (primitives first; checks interleaved with
+    # posing, either way round): the same verdicts in both modes, and for
+    # states
     states = q0[: min(n, 20000)]
     want_s = val.validate_states(states).cpu().numpy()
-    val.set_check_order(1)
-    assert val.check_order() == 1
-    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
-        got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
-        assert np.array_equal(got, want), mode
-    assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s)
+    for order in (1, 2, 3):
+        val.set_check_order(order)
+        assert val.check_order() == order
+        for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
+            got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
+            assert np.array_equal(got, want), (order, mode)
+        got, work = val.validate_edges_work(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED)
+        assert np.array_equal(got.cpu().numpy(), want), order
+        assert int(work[vp.VP_WORK_EDGES_DONE]) == n
+        assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s), order
     val.set_check_order(0)
     assert val.sync_status()[0] == vp.VP_OK
     with pytest.raises(vp.VPError):
         val.set_screen_rounds(-1)
-    with pytest.raises(vp.VPError):
-        val.set_check_order(2)
+    for bad in (-1, 4):
+        with pytest.raises(vp.VPError):
+            val.set_check_order(bad)
     val.close()
 
 

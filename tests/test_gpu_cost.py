@@ -1,9 +1,14 @@
 """Penetration cost and its reverse-mode FK adjoint against the FP64 oracle.
 
-Bars: cost within rtol 1e-4 (+1e-6 absolute); gradient within 1e-3 of the
-oracle's analytic gradient relative to the sample's largest component, plus
-an absolute floor of 5e-5 that covers float32 rounding of positions (about
-1e-6 m) times a lever arm of a metre or two over a few dozen active terms.
+Bars:
+- cost within rtol 1e-4 (+1e-6 absolute);
+- gradient, per sample: max_j |g_gpu,j - g_ref,j| <= 1e-3 * max_j |g_ref,j|
+  on every sample whose root-sum-square penetration sqrt(cost) exceeds the
+  1e-4 m clearance band the verdicts use.  Within the band the float32
+  sphere positions (rounded to about 1e-7 m) decide the penetration depth
+  itself, so a relative bar cannot hold; there the error must stay below
+  1e-3 of the gradient a penetration at the band's edge gives (2e-7), and
+  those samples are counted.
 Samples within reach of a kink of the distance (the oracle's central
 differences at h and 2h disagree) are skipped and counted."""
 import numpy as np
@@ -16,6 +21,7 @@ import vpgen
 pytestmark = pytest.mark.gpu
 
 MARGIN = 0.02
+BAND = oracle.BAND  # 1e-4 m
 
 
 @pytest.fixture(scope="module")
@@ -45,27 +51,39 @@ def _kinky(o, q, margin):
 
 
 def _check(val, o, q, margin):
+    """Check cost and gradient on every sample; returns (kink, band, pinned)
+    sample counts."""
     c_gpu, g_gpu = val.collision_cost(torch.from_numpy(q).cuda(), margin, grad=True)
     c_gpu, g_gpu = c_gpu.cpu().numpy().astype(np.float64), g_gpu.cpu().numpy().astype(np.float64)
     c_ref, g_ref = o.cost(q.astype(np.float64), margin)
     np.testing.assert_allclose(c_gpu, c_ref, rtol=1e-4, atol=1e-6)
     kink = _kinky(o, q.astype(np.float64), margin)
-    ok = ~kink
-    scale = np.abs(g_ref).max(axis=1, keepdims=True)
-    err = np.abs(g_gpu - g_ref)
-    assert np.all(err[ok] <= 1e-3 * scale[ok] + 5e-5), float((err - 1e-3 * scale).max())
-    rel = (err.max(axis=1) / np.maximum(scale[:, 0], 1e-12))[ok & (c_ref > 1e-4)]
-    return kink.mean(), rel
+    pen = np.sqrt(c_ref)
+    pinned = ~kink & (pen > BAND)
+    band = ~kink & ~pinned
+    scale = np.abs(g_ref).max(axis=1)
+    err = np.abs(g_gpu - g_ref).max(axis=1)
+    rel = err[pinned] / scale[pinned]
+    assert np.all(rel <= 1e-3), f"{int((rel > 1e-3).sum())} samples, worst {rel.max():.3e}"
+    assert np.all(err[band] <= 1e-3 * 2 * BAND), float(err[band].max())
+    print(f"{q.shape[0]} samples: {int(pinned.sum())} checked at relative 1e-3 (worst {rel.max():.2e}), "
+          f"{int((band & (c_ref > 0)).sum())} penetrating within the band, {int(kink.sum())} near a kink")
+    return int(kink.sum()), int(band.sum()), int(pinned.sum())
 
 
 def test_cost_and_gradient_mixed_scene(vpmod):
+    """Every one of the 65,536 configurations of the mixed-primitive scene,
+    and a 16,384-waypoint subset of its 4,096 straight 64-waypoint paths."""
     Validator, _, _ = vpmod
-    w = vpgen.workload(vpgen.ARM7_MIXED128, n_edges=2048)
+    w = vpgen.workload(vpgen.ARM7_MIXED128)
     val = Validator(w.robot, w.env)
     o = oracle.Oracle(w.robot, w.env)
-    kink_frac, rel = _check(val, o, w.q0, MARGIN)
-    assert kink_frac < 0.05
-    assert (rel <= 1e-3).mean() > 0.95  # the pure relative bar holds on samples with real penetration
+    kinks, band, pinned = _check(val, o, w.q0, MARGIN)
+    assert kinks < 0.01 * w.q0.shape[0] and pinned > 0.3 * w.q0.shape[0]
+    paths = vpgen.straight_paths(w.robot, 4096, 64, seed=303).reshape(-1, w.robot.dof)
+    sub = paths[np.random.default_rng(303).choice(paths.shape[0], 16384, replace=False)]
+    kinks, band, pinned = _check(val, o, np.ascontiguousarray(sub), MARGIN)
+    assert kinks < 0.01 * sub.shape[0] and pinned > 0.3 * sub.shape[0]
 
 
 def test_gradient_tree_prismatic_general_axes(vpmod):
@@ -81,9 +99,9 @@ def test_gradient_tree_prismatic_general_axes(vpmod):
                     np.array([np.concatenate([[0.2, 0.0, -0.1], np.eye(3).ravel(), [0.2, 0.15, 0.1]])]))
     val = Validator(r, env)
     o = oracle.Oracle(r, env)
-    q = rng.uniform(-1.5, 1.5, size=(1024, 9)).astype(np.float32)
-    kink_frac, rel = _check(val, o, q, MARGIN)
-    assert kink_frac < 0.1
+    q = rng.uniform(-1.5, 1.5, size=(4096, 9)).astype(np.float32)
+    kinks, band, pinned = _check(val, o, q, MARGIN)
+    assert kinks < 0.1 * q.shape[0] and pinned > 0.3 * q.shape[0]
 
 
 def test_cost_zero_and_no_grad(vpmod):
