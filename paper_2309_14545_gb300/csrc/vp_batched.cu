@@ -2,7 +2,10 @@
 //
 // 1. bucket_count_kernel: state count k_e of every edge (explicit or from the
 //    resolution), bucket = ceil(log2 k) class ([2,4], [5,8], ..., [257,512],
-//    >512), block-aggregated histogram.  Malformed edges are answered here.
+//    >512), block-aggregated histogram.  Malformed counts (and, without
+//    explicit counts, non-finite or over-long edges) are answered here; with
+//    explicit counts the endpoints are read only once, by the edge kernel,
+//    which answers a non-finite endpoint.
 // 2. bucket_scatter_kernel: a permutation listing edges bucket by bucket,
 //    longest bucket first (longest-processing-time order for the queue).
 // 3. edges_batched_kernel: persistent; each warp pops work items from one
@@ -39,15 +42,10 @@ __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, c
     __syncthreads();
     const long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < E) {
-        float dmax = 0.f;
-        bool fin = true;
-        for (int j = 0; j < D; ++j) {
-            const float a = q0[e * D + j], b = q1[e * D + j];
-            fin &= isfinite(a) && isfinite(b);
-            if (fin) dmax = fmaxf(dmax, fabsf(b - a));
-        }
         int k = -1;
         if (counts != nullptr) {
+            // explicit counts: the endpoints are not read here (the edge
+            // kernel checks that they are finite as it loads them)
             k = counts[e];
             if (k < 2) {
                 atomicOr(status, VP_DEVERR_COUNT);
@@ -56,11 +54,19 @@ __global__ void bucket_count_kernel(const int D, const float *__restrict__ q0, c
                 atomicOr(status, VP_DEVERR_LENGTH);
                 k = -1;
             }
-        } else if (fin) {
-            k = count_from_dmax(dmax, res);
-            if (k < 0) atomicOr(status, VP_DEVERR_LENGTH);
+        } else {
+            float dmax = 0.f;
+            bool fin = true;
+            for (int j = 0; j < D; ++j) {
+                const float a = q0[e * D + j], b = q1[e * D + j];
+                fin &= isfinite(a) && isfinite(b);
+                if (fin) dmax = fmaxf(dmax, fabsf(b - a));
+            }
+            if (fin) {
+                k = count_from_dmax(dmax, res);
+                if (k < 0) atomicOr(status, VP_DEVERR_LENGTH);
+            }
         }
-        if (!fin) k = -1;
         kbuf[e] = k;
         if (k < 0)
             valid[e] = 0;

@@ -248,11 +248,14 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         const int e = ek.x, k = ek.y;
         float *gq0 = wbuf + g * 32, *gdq = gq0 + 16;
         __syncwarp();
+        bool fin = true;
         if (has_edge) {
             for (int d = j; d < D; d += G) {
                 const float a = q0[static_cast<long long>(e) * D + d];
+                const float b = q1[static_cast<long long>(e) * D + d];
+                fin &= isfinite(a) && isfinite(b);
                 gq0[d] = a;
-                gdq[d] = q1[static_cast<long long>(e) * D + d] - a;
+                gdq[d] = b - a;
             }
         } else {
             for (int d = j; d < 16; d += G) {
@@ -261,11 +264,19 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
             }
         }
         __syncwarp();
+        // an edge with a non-finite endpoint coordinate is invalid (its group
+        // takes no state); with counts from the resolution the count pass has
+        // answered it already
+        const bool group_fin = (__ballot_sync(kFull, !fin) & gmask) == 0u;
+        if (has_edge && !group_fin && j == 0) {
+            valid[e] = 0;
+            if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
+        }
         const int R = (k + G - 1) / G;
         const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
-        const int R_max = __reduce_max_sync(kFull, has_edge ? R : 0);
+        const int R_max = __reduce_max_sync(kFull, has_edge && group_fin ? R : 0);
         const int R_lim = plan.screen_rounds > 0 ? min(R_max, plan.screen_rounds) : R_max;
-        bool done = !has_edge;
+        bool done = !has_edge || !group_fin;
         for (int r = 0; r < R_lim; ++r) {
             int i = j * R + r;
             const WorkRef<STATS> w{&wk, !done && i < k};

@@ -73,24 +73,42 @@ def test_batched_mixed_lengths_against_oracle(vpmod):
 
 
 def test_batched_edge_cases(vpmod):
-    """Bad counts and non-finite endpoints are answered in the bucketing
-    pass (invalid + device status); tiny and empty batches; new buffers
-    after a graph was built."""
+    """Bad counts are answered in the bucketing pass (invalid + device
+    status); non-finite endpoints make an edge invalid -- in the edge kernel
+    with explicit counts (in every length bucket, so at every lane-group
+    size), in the bucketing pass without; tiny and empty batches; new
+    buffers after a graph was built."""
     Validator, vp = vpmod
     w = vpgen.workload(vpgen.DUAL14_SHELVES, n_edges=70)
     val = Validator(w.robot, w.env)
     counts = w.counts.copy()
     counts[3] = 0
-    q0 = w.q0.copy()
+    q0, q1 = w.q0.copy(), w.q1.copy()
     q0[5, 2] = np.nan
-    got = val.validate_edges(_cuda(q0), _cuda(w.q1), _cuda(counts), float(w.res), mode=vp.VP_MODE_BATCHED)
+    q1[6, 13] = np.inf
+    q0[7, 0] = -np.inf
+    bad = [5, 6, 7]
+    for i, k in zip(range(8, 17), (2, 5, 9, 17, 33, 65, 129, 257, 512)):  # one per bucket
+        counts[i] = k
+        q1[i, i % 14] = np.nan
+        bad.append(i)
+    got = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), float(w.res), mode=vp.VP_MODE_BATCHED)
     st, bits = val.sync_status()
-    assert st == vp.VP_ERR_DEVICE and bits & vp.VP_DEVERR_COUNT
+    assert st == vp.VP_ERR_DEVICE and bits == vp.VP_DEVERR_COUNT
     got = got.cpu().numpy()
-    assert got[3] == 0 and got[5] == 0
-    plain = val.validate_edges(_cuda(q0), _cuda(w.q1), _cuda(counts), float(w.res)).cpu().numpy()
+    assert got[3] == 0 and np.all(got[bad] == 0)
+    plain = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), float(w.res)).cpu().numpy()
     val.sync_status()
     assert np.array_equal(got, plain)
+    for lanes in ([4] * 9, [32] * 9):
+        val.set_tiling(lanes)
+        again = val.validate_edges(_cuda(q0), _cuda(q1), _cuda(counts), float(w.res), mode=vp.VP_MODE_BATCHED)
+        val.sync_status()
+        assert np.array_equal(again.cpu().numpy(), plain), lanes
+    got = val.validate_edges(_cuda(q0), _cuda(q1), None, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+    assert val.sync_status()[0] == vp.VP_OK
+    assert np.all(got[bad] == 0)
+    assert np.array_equal(got, val.validate_edges(_cuda(q0), _cuda(q1), None, float(w.res)).cpu().numpy())
     for n in (1, 2, 33):
         a = val.validate_edges(_cuda(w.q0[:n]), _cuda(w.q1[:n]), _cuda(w.counts[:n]), float(w.res),
                                mode=vp.VP_MODE_BATCHED).cpu().numpy()
