@@ -231,9 +231,16 @@ vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, 
 vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin, float *cost,
                             float *grad, void *stream);
 
-/* Tune the batched mode's tiling on a sample of edges (runs kernels and
- * synchronises `stream`).  The choice is cached in the context per robot,
- * environment and edge-length profile. */
+/* Tune the batched mode on a sample of edges (runs kernels and synchronises
+ * the device).  First it counts, on the batch's first (up to) 65,536 start
+ * configurations, how often each self-pair link pair and each primitive
+ * collides with the robot, and orders both most often first: the link pairs
+ * for VP_ORDER_FREQUENT, the primitives (within each kind, and the kinds by
+ * their totals) for every check order -- a state that collides then meets
+ * its collision sooner.  Then it chooses the tiling, the screening rounds and
+ * the check order by timing whole launches.  The choice is cached in the
+ * context per robot, environment and edge-length profile.  The verdicts do
+ * not depend on any of it. */
 vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                       float resolution, int64_t n_edges, void *stream);
 
@@ -276,8 +283,8 @@ vp_status vp_set_tiling(vp_ctx *ctx, const int32_t *lanes, int n);
 vp_status vp_set_screen_rounds(vp_ctx *ctx, int rounds);
 vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
 
-/* Check order of the validation kernels (edges and states, every mode), a
- * combination of two bits:
+/* Check order of the validation kernels (edges and states, every mode):
+ * VP_ORDER_FREQUENT, or a combination of two bits:
  *   VP_ORDER_PRIMS_FIRST: primitives (link bounding spheres, then fine
  *     spheres) before self pairs; without it, self pairs first;
  *   VP_ORDER_INTERLEAVE: checks interleaved with posing, the paper's order
@@ -285,13 +292,19 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
  *     it is posed (its self pairs with earlier links, and its spheres against
  *     the primitives), so that links after a collision are never posed;
  *     without it, every link is posed first and the checks run after.
+ * VP_ORDER_FREQUENT (4): the link pairs that collide most often first (as
+ *   vp_autotune counted them; before that, their packed order) -- those
+ *   that hold three quarters of the counted collisions -- with each link
+ *   posed only when a check first needs it; then primitives; then the
+ *   remaining link pairs.
  * 0 (the default) is "pose all, self pairs first".  Which order finds a
  * colliding configuration with the least work depends on the robot and the
- * scene; vp_autotune times all four.  vp_set_check_order pins one
- * (VP_ERR_ARG outside 0..3) until the next vp_autotune or load.  The
+ * scene; vp_autotune times all five.  vp_set_check_order pins one
+ * (VP_ERR_ARG outside 0..4) until the next vp_autotune or load.  The
  * verdicts do not depend on it. */
 #define VP_ORDER_PRIMS_FIRST 0x1
 #define VP_ORDER_INTERLEAVE 0x2
+#define VP_ORDER_FREQUENT 0x4
 vp_status vp_set_check_order(vp_ctx *ctx, int order);
 vp_status vp_check_order(vp_ctx *ctx, int *order);
 

@@ -31,8 +31,12 @@ def _deps():
 
 # The files that define the edge-validation kernels (device code, tables and
 # their layouts); host-side launch code, the tuner and other kernels are not.
-KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_inst_l8.cu", "vp_inst_l9.cu",
-                "vp_inst_l15.cu", "vp_inst_l17.cu", "vp_api.cu")
+KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_inst.cu", "vp_api.cu")
+
+# vp_inst.cu holds the validation kernels of one link bound and one family of
+# check orders per compilation: it is compiled once for each pair.
+INST_LMAX = (8, 9, 15, 17)
+INST_FAMILIES = (0, 1, 2)
 
 
 def _code_only(text: str) -> str:
@@ -69,12 +73,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return OUT
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    inst = os.path.join(CSRC, "vp_inst.cu")
+    units = [(p, ()) for p in sorted(glob.glob(os.path.join(CSRC, "*.cu"))) if p != inst]
+    units += [(inst, (f"-DVP_INST_LMAX={l}", f"-DVP_INST_FAM={f}")) for l in INST_LMAX for f in INST_FAMILIES]
+    # the slowest units first, so that they start at once
+    units.sort(key=lambda u: (u[0] != inst, u[0]))
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + f".{os.getpid()}.o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, defs = unit
+        tag = os.path.basename(src) + "".join(d.split("=")[-1] for d in defs)
+        obj = os.path.join(BUILD, tag + f".{os.getpid()}.o")
+        cmd = [nvcc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -84,8 +94,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    with ThreadPoolExecutor(max_workers=min(len(units), max(4, os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = OUT + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     for o in objs:

@@ -24,6 +24,7 @@ struct vp_ctx {
     bool robot_loaded = false;
     std::vector<uint16_t> sorted_of;  // caller's sphere index -> sorted index
     float4 *env_buf = nullptr;
+    std::vector<float4> env_host;  // the packed environment as on the device (visiting order)
     EnvView env{};
     uint64_t env_hash = 0;       // contents of the packed environment (tuning-cache key)
     bool env_loaded = false;
@@ -445,6 +446,8 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         rp.joints[j].meta |= (pl & 0xFF) << kMetaParentLinkShift;
     }
     rp.n_groups = ng;
+    for (int g = 0; g < kMaxGroups; ++g) rp.gorder[g] = static_cast<uint8_t>(g < ng ? g : 0);
+    rp.n_gfront = ng;
     rp.n_slots = n_slots;
     rp.link_mask = 0;
     for (int l = 0; l < L; ++l)
@@ -469,6 +472,14 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
 
 // ---------------------------------------------------------------------------
 // environment
+
+// FNV-1a over the packed environment's bytes (the tuning cache's key).
+static uint64_t packed_hash(const std::vector<float4> &h) {
+    uint64_t hsh = 1469598103934665603ull;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(h.data());
+    for (size_t i = 0; i < h.size() * 16; ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+    return hsh;
+}
 
 extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
     if (!ctx) return VP_ERR_ARG;
@@ -498,12 +509,8 @@ extern "C" vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *e) {
     ctx->env_buf = buf;
     view.data = buf;
     ctx->env = view;
-    {  // FNV-1a over the packed bytes
-        uint64_t hsh = 1469598103934665603ull;
-        const unsigned char *b = reinterpret_cast<const unsigned char *>(h.data());
-        for (size_t i = 0; i < n4 * 16; ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
-        ctx->env_hash = hsh;
-    }
+    ctx->env_hash = packed_hash(h);
+    ctx->env_host = std::move(h);
     ctx->env_loaded = true;
     batched_invalidate(ctx->batched);
     return VP_OK;
@@ -650,10 +657,11 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
     cudaError_t e = cudaSuccess;
     const bool stats = work != nullptr, simple = ctx->robot.simple != 0;
     const int lmax = lmax_for(ctx->robot.n_links);
+    const int order = batched_check_order(ctx->batched);
     if (!plan_launch(
             ctx,
-            [stats, lmax, simple](size_t sm, int b, bool staged, int *o) {
-                return prepare_edges_plain(stats, lmax, simple, staged, sm, b, o);
+            [stats, lmax, simple, order](size_t sm, int b, bool staged, int *o) {
+                return prepare_edges_plain(stats, lmax, simple, staged, sm, b, o, order);
             },
             &view, &block, &smem, &bps, &e))
         return fail(ctx, VP_ERR_CAPACITY, "frame stash exceeds shared memory");
@@ -717,10 +725,37 @@ extern "C" vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, 
     if (!counts && (!(resolution > 0.f) || !std::isfinite(resolution)))
         return fail(ctx, VP_ERR_ARG, "resolution must be > 0 when counts is NULL");
     DeviceGuard g(ctx->device);
-    BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, nullptr, ctx->status,
-                  ctx->num_sms, ctx->smem_optin, static_cast<cudaStream_t>(stream)};
-    a.env_hash = ctx->env_hash;
     std::string msg;
+    // the frequent-first order of the self-pair groups, counted on the
+    // batch's first start configurations (a sample of its states)
+    const int64_t n_sample = std::min<int64_t>(n_edges, 65536);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (ctx->robot.n_groups > 0 &&
+        group_order(ctx->robot, q0, n_sample, st, ctx->robot.gorder, &ctx->robot.n_gfront, &msg) != 0)
+        return fail(ctx, VP_ERR_CUDA, "vp_autotune: %s", msg.c_str());
+    // the environment's visiting order: each kind's primitives most often
+    // touched first, the kinds by their total (counted on the same sample)
+    if (!ctx->env_host.empty()) {
+        std::vector<unsigned> hits;
+        if (prim_hits(ctx->robot, ctx->env, q0, n_sample, st, &hits, &msg) != 0)
+            return fail(ctx, VP_ERR_CUDA, "vp_autotune: %s", msg.c_str());
+        std::vector<float4> re;
+        EnvView view = ctx->env;
+        reorder_env(ctx->env_host, hits, &view, &re);
+        if (re.size() != ctx->env_host.size() ||
+            std::memcmp(re.data(), ctx->env_host.data(), re.size() * sizeof(float4)) != 0 ||
+            view.kind_order != ctx->env.kind_order) {
+            cudaError_t e = cudaDeviceSynchronize();  // queued work may still read the buffer
+            if (e == cudaSuccess) e = cudaMemcpy(ctx->env_buf, re.data(), re.size() * 16, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_autotune (environment order)");
+            ctx->env = view;
+            ctx->env_hash = packed_hash(re);
+            ctx->env_host = std::move(re);
+        }
+    }
+    BatchedArgs a{&ctx->robot, &ctx->env, q0, q1, counts, resolution, n_edges, nullptr, ctx->status,
+                  ctx->num_sms, ctx->smem_optin, st};
+    a.env_hash = ctx->env_hash;
     const int rc = batched_autotune(ctx->batched, a, &msg);
     if (rc == 0) return VP_OK;
     return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "vp_autotune: %s", msg.c_str());
@@ -823,7 +858,7 @@ vp_status vp_link_bounds(vp_ctx *ctx, int n_links, float *link_sphere, float *ha
 
 extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int order) {
     if (!ctx) return VP_ERR_ARG;
-    if (order < 0 || order >= kOrderCount) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 to 3");
+    if (order < 0 || order >= kOrderCount) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 to 4");
     batched_set_check_order(ctx->batched, order);
     return VP_OK;
 }

@@ -99,12 +99,12 @@ __global__ void bucket_scatter_kernel(const long long E, const int32_t *__restri
     if (b >= 0) perm[off[b] + base[b] + r] = make_int2(static_cast<int>(e), k);
 }
 
-BatchedKernel batched_kernel_for(const RobotParams &P, bool stats, bool staged) {
-    return kernel_set(lmax_for(P.n_links)).batched[stats][P.simple != 0][staged];
+BatchedKernel batched_kernel_for(const RobotParams &P, bool stats, bool staged, int order) {
+    return kernel_set(lmax_for(P.n_links)).batched[family_of(order)][stats][P.simple != 0][staged];
 }
 
-SurvivorsKernel survivors_kernel_for(const RobotParams &P, bool stats, bool staged) {
-    return kernel_set(lmax_for(P.n_links)).survivors[stats][P.simple != 0][staged];
+SurvivorsKernel survivors_kernel_for(const RobotParams &P, bool stats, bool staged, int order) {
+    return kernel_set(lmax_for(P.n_links)).survivors[family_of(order)][stats][P.simple != 0][staged];
 }
 
 size_t batched_smem(const EnvView &env, const RobotParams &P) {
@@ -206,22 +206,32 @@ int prepare_kernel(const BatchedArgs &a, EnvView *view, size_t *smem, int *grid,
     }
     const size_t m_max = m_st <= a.smem_optin ? m_st : m_in;
     cudaError_t e = cudaSuccess;
-    for (int stats = 0; stats < 2; ++stats)
-        for (int staged = 0; staged < 2; ++staged) {
-            const void *k[2] = {reinterpret_cast<const void *>(batched_kernel_for(*a.robot, stats, staged)),
-                                reinterpret_cast<const void *>(survivors_kernel_for(*a.robot, stats, staged))};
-            const size_t m = staged ? m_max : m_in;
-            for (const void *f : k)
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m));
-        }
+    // every family of check orders (the tuner switches between them); the
+    // grid fills the SMs for the family that keeps the most blocks resident
+    // (blocks past another family's residency start late and find the queue
+    // drained)
     int b_in = 0, b_st = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_in, batched_kernel_for(*a.robot, false, false), kBlock,
-                                                          m_in);
-    if (e == cudaSuccess && m_st <= a.smem_optin)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b_st, batched_kernel_for(*a.robot, false, true), kBlock,
-                                                          m_st);
+    for (int fam = 0; fam < kFamCount; ++fam) {
+        const int order = fam == kFamFrequent ? kOrderFrequent : (fam == kFamInterleave ? kOrderInterleave : 0);
+        for (int stats = 0; stats < 2; ++stats)
+            for (int staged = 0; staged < 2; ++staged) {
+                const void *k[2] = {reinterpret_cast<const void *>(batched_kernel_for(*a.robot, stats, staged, order)),
+                                    reinterpret_cast<const void *>(survivors_kernel_for(*a.robot, stats, staged, order))};
+                const size_t m = staged ? m_max : m_in;
+                for (const void *f : k)
+                    if (e == cudaSuccess)
+                        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m));
+            }
+        int bi = 0, bs = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, batched_kernel_for(*a.robot, false, false, order),
+                                                              kBlock, m_in);
+        if (e == cudaSuccess && m_st <= a.smem_optin)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, batched_kernel_for(*a.robot, false, true, order),
+                                                              kBlock, m_st);
+        b_in = std::max(b_in, bi);
+        b_st = std::max(b_st, bs);
+    }
     if (e != cudaSuccess) return set_err(msg, "batched kernel attributes", e);
     const bool staged = b_st >= 1 && b_st >= b_in;
     *view = staged ? vst : vin;
@@ -247,12 +257,12 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const B
     // external event-record nodes, so the events time the kernel when replayed from the graph
     if (a.ev_start) e = cudaEventRecordWithFlags(a.ev_start, s, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    batched_kernel_for(*a.robot, work != nullptr, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
+    batched_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
                                                                             plan, valid, a.status, im->ctrl, im->surv,
                                                                             work);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    survivors_kernel_for(*a.robot, work != nullptr, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+    survivors_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
                                                                               plan, valid, a.status, im->ctrl, work);
     e = cudaGetLastError();
     if (e == cudaSuccess && a.ev_stop) e = cudaEventRecordWithFlags(a.ev_stop, s, cudaEventRecordExternal);
@@ -428,10 +438,10 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
             e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, 3 * sizeof(int), s);  // both queues, survivor count
             if (e != cudaSuccess) break;
             cudaEventRecord(t0, s);
-            batched_kernel_for(*a.robot, false, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
+            batched_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
                                                                            p, tv, a.status, im->ctrl, im->surv,
                                                                            nullptr);
-            survivors_kernel_for(*a.robot, false, view.staged)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+            survivors_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
                                                                              p, tv, a.status, im->ctrl, nullptr);
             cudaEventRecord(t1, s);
             e = cudaEventSynchronize(t1);

@@ -39,22 +39,23 @@ using BatchedKernel = void (*)(RobotParams, EnvView, const float *, const float 
 using SurvivorsKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
                                  uint8_t *, unsigned *, int *, unsigned long long *);
 struct KernelSet {
-    PlainKernel plain[2][2][2];          // [stats][simple][staged]
-    BatchedKernel batched[2][2][2];
-    SurvivorsKernel survivors[2][2][2];
+    PlainKernel plain[3][2][2][2];  // [family][stats][simple][staged]
+    BatchedKernel batched[3][2][2][2];
+    SurvivorsKernel survivors[3][2][2][2];
 };
-const KernelSet &kernel_set_l8();
-const KernelSet &kernel_set_l9();
-const KernelSet &kernel_set_l15();
-const KernelSet &kernel_set_l17();
-inline const KernelSet &kernel_set(int lmax) {
-    switch (lmax) {
-        case 8: return kernel_set_l8();
-        case 9: return kernel_set_l9();
-        case 15: return kernel_set_l15();
-        default: return kernel_set_l17();
-    }
-}
+// The instances of one link bound and family, each from its own compilation
+// of vp_inst.cu.
+#define VP_DECLARE_FILL(L)                    \
+    void kernel_set_fill_l##L##_f0(KernelSet &); \
+    void kernel_set_fill_l##L##_f1(KernelSet &); \
+    void kernel_set_fill_l##L##_f2(KernelSet &);
+VP_DECLARE_FILL(8)
+VP_DECLARE_FILL(9)
+VP_DECLARE_FILL(15)
+VP_DECLARE_FILL(17)
+#undef VP_DECLARE_FILL
+// Every instance of link bound lmax (8, 9, 15 or 17).
+const KernelSet &kernel_set(int lmax);
 
 struct BatchedArgs {
     const RobotParams *robot;

@@ -732,6 +732,139 @@ __device__ __forceinline__ bool pose_and_check_interleaved(const RobotParams &P,
     return col;
 }
 
+// On-demand posing for the frequent-first order: the joints whose motion
+// parameters are stashed (posed) and the links whose bounding-sphere centres
+// are stashed (centred), warp-uniform bit masks.  ensure() poses the joints
+// on the path to link l that are not posed yet -- walking the path from the
+// base (joints are numbered parents first) -- and stashes the centre of
+// every sphere-carrying link it passes.
+struct LazyPose {
+    unsigned posed = 0, centred = 0;
+};
+
+template <bool SIMPLE, bool STATS, class QF>
+__device__ __forceinline__ void ensure_link(const RobotParams &P, int l, const QF &qf, const Stash &stash,
+                                            LazyPose &lp, const WorkRef<STATS> &w) {
+    if ((lp.centred >> l) & 1u) return;
+    Fr f;
+    fr_identity(f);
+    const LinkC &L0 = P.links[0];
+    if (!(lp.centred & 1u) && L0.s0 < L0.s1) {  // the base link: identity frame
+        stash.store_centre(0, make_float3(L0.bs.x, L0.bs.y, L0.bs.z));
+        w.add(VP_WORK_LINK_CENTRES, 1);
+    }
+    lp.centred |= 1u;
+    unsigned m = P.links[l].path;
+#pragma unroll 1
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const JointC &J = P.joints[j];
+        float ms, mc;
+        if ((lp.posed >> j) & 1u) {
+            ms = stash.mo(j, 0);
+            mc = stash.mo(j, 1);
+        } else {
+            joint_motion(J, qf(j), ms, mc);
+            stash.mo(j, 0) = ms;
+            stash.mo(j, 1) = mc;
+            lp.posed |= 1u << j;
+        }
+        apply_joint_sc<SIMPLE>(J, ms, mc, f);
+        const int lj = j + 1;
+        if (!((lp.centred >> lj) & 1u)) {
+            const LinkC &L = P.links[lj];
+            if (L.s0 < L.s1) {
+                stash.store_centre(lj, fr_apply(f, L.bs.x, L.bs.y, L.bs.z));
+                w.add(VP_WORK_LINK_CENTRES, 1);
+            }
+            lp.centred |= 1u << lj;
+        }
+    }
+}
+
+// Self-pair groups gorder[gi0 .. gi1) for the frequent-first order, each
+// link posed when a group first needs it.  Returns the warp's stop decision.
+template <int MODE, bool STATS, bool SIMPLE, class QF>
+__device__ __forceinline__ bool frequent_groups(const RobotParams &P, int gi0, int gi1, const QF &qf,
+                                                const Stash &stash, LazyPose &lp, FrameCursor &cur_a,
+                                                FrameCursor &cur_b, Ctl &ctl, bool &col, const WorkRef<STATS> &w) {
+#pragma unroll 1
+    for (int gi = gi0; gi < gi1; ++gi) {
+        const GroupC G = P.groups[P.gorder[gi]];
+        ensure_link<SIMPLE>(P, G.la, qf, stash, lp, w);
+        ensure_link<SIMPLE>(P, G.lb, qf, stash, lp, w);
+        const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
+        const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+        const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
+        const bool h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+        if (!ctl.idle) w.add(VP_WORK_PAIR_COARSE, 1);
+        if (!__any_sync(kFull, wants(ctl, h))) continue;
+        const Fr &fb = frame_at<SIMPLE>(P, G.lb, stash, cur_b);
+        const Fr &fa = frame_at<SIMPLE>(P, G.la, stash, cur_a);
+        w.slot(VP_WORK_LANE_PAIR_FINE, G.p1 - G.p0);
+        if (!ctl.idle) w.add(VP_WORK_PAIR_FINE, G.p1 - G.p0);
+        if (!ctl.idle && h) w.add(VP_WORK_PAIR_FINE_OWN, G.p1 - G.p0);
+#pragma unroll 1
+        for (int p = G.p0; p < G.p1; ++p) {
+            const PairC pr = P.pairs[p];
+            const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
+            const float3 a = fr_apply(fa, sa.x, sa.y, sa.z);
+            const float3 b = fr_apply(fb, sb.x, sb.y, sb.z);
+            const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+            const float r2 = sa.w + sb.w;
+            col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
+        }
+        if (group_stop<MODE>(ctl, col)) return true;
+    }
+    return false;
+}
+
+// The frequent-first order: the link pairs that collide most often
+// (RobotParams::gorder, counted on a sample; the first n_gfront of them),
+// each link posed only when a pair first needs it, so that a state that
+// collides there poses only those links' paths; then, if the state is still
+// free, every remaining link is posed and the primitives are checked as in
+// pose_and_check_all; then the remaining link pairs.  Verdicts equal those
+// of the other orders.
+template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+__device__ __forceinline__ bool pose_and_check_frequent(const RobotParams &P, const QF &qf, const EnvSm &env,
+                                                        const Stash &stash, const Ctl &ctl_in,
+                                                        const WorkRef<STATS> &w) {
+    bool col = false;
+    Ctl ctl = ctl_in;
+    w.add(VP_WORK_STATES, 1);
+    w.slot(VP_WORK_LANE_STATES, 1);
+    LazyPose lp;
+    FrameCursor cur_a, cur_b;
+    if (frequent_groups<MODE, STATS, SIMPLE>(P, 0, P.n_gfront, qf, stash, lp, cur_a, cur_b, ctl, col, w)) return col;
+    // primitives: every sphere-carrying link posed, then as pose_and_check_all
+#pragma unroll 1
+    for (int l = 0; l < P.n_links; ++l)
+        if (((P.link_mask >> l) & 1u) && !((lp.centred >> l) & 1u)) ensure_link<SIMPLE>(P, l, qf, stash, lp, w);
+    {
+        const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
+        FrameCursor fc;
+#pragma unroll 1
+        for (int ki = 0; ki < 3; ++ki) {
+            const int kind = (env.kind_order >> (4 * ki)) & 15;
+            bool stop;
+            if (kind == 0)
+                stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl, col,
+                                                            w);
+            else if (kind == 1)
+                stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl, col,
+                                                            w);
+            else
+                stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl, col,
+                                                            w);
+            if (stop) return col;
+        }
+    }
+    frequent_groups<MODE, STATS, SIMPLE>(P, P.n_gfront, P.n_groups, qf, stash, lp, cur_a, cur_b, ctl, col, w);
+    return col;
+}
+
 // Pose one configuration and check it (Sec. III-B/C/D):
 //   1. pose every link (FK is cheap next to the checks), keeping each
 //      joint's (sin, cos) and the world centre of each link's bounding
@@ -741,8 +874,7 @@ __device__ __forceinline__ bool pose_and_check_interleaved(const RobotParams &P,
 //   3. primitives, kind by kind, each against every link's bounding sphere
 //      (pairs first culled by warp-wide boxes, see prim_pass), then fine
 //      spheres where a coarse test hit.
-// Steps 2 and 3 swap when the environment view says so (kOrderPrimsFirst);
-// with kOrderInterleave the state goes to pose_and_check_interleaved.
+// Steps 2 and 3 swap when the environment view says so (kOrderPrimsFirst).
 // Frames needed by fine tests are recomputed from the kept (sin, cos).  The
 // order of checks is chosen for early exit: a colliding configuration is
 // most often found by a self pair or a large primitive; it does not change
@@ -750,10 +882,8 @@ __device__ __forceinline__ bool pose_and_check_interleaved(const RobotParams &P,
 // per-link loops and the cull's lane layout).
 // Returns this lane's collision flag; the warp stops early per MODE.
 template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
-__device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
-                                               const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w) {
-    if (env.order & kOrderInterleave)
-        return pose_and_check_interleaved<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl_in, w);
+__device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const QF &qf, const EnvSm &env,
+                                                   const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w) {
     bool col = false;
     Ctl ctl = ctl_in;
     const int D = P.n_joints;
@@ -841,6 +971,39 @@ __device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &q
         }
     }
     return col;
+}
+
+// Kernel families: each edge kernel is instantiated once per family of
+// check orders, so that each holds the code (and the registers) of one
+// order only.
+enum : int { kFamPoseAll = 0, kFamInterleave = 1, kFamFrequent = 2, kFamCount = 3 };
+
+__host__ __device__ __forceinline__ int family_of(int order) {
+    return order == kOrderFrequent ? kFamFrequent : ((order & kOrderInterleave) ? kFamInterleave : kFamPoseAll);
+}
+
+// One state checked in the order of family FAM (the prims-first bit of
+// env.order still applies within it).
+template <int FAM, int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+__device__ __forceinline__ bool check_state(const RobotParams &P, const QF &qf, const EnvSm &env, const Stash &stash,
+                                            const Ctl &ctl, const WorkRef<STATS> &w) {
+    if constexpr (FAM == kFamFrequent)
+        return pose_and_check_frequent<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+    else if constexpr (FAM == kFamInterleave)
+        return pose_and_check_interleaved<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+    else
+        return pose_and_check_all<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+}
+
+// The same with the family chosen at run time from env.order (one kernel
+// holding every order: state validation).
+template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+__device__ __forceinline__ bool pose_and_check(const RobotParams &P, const QF &qf, const EnvSm &env,
+                                               const Stash &stash, const Ctl &ctl, const WorkRef<STATS> &w) {
+    const int fam = family_of(env.order);
+    if (fam == kFamFrequent) return check_state<kFamFrequent, MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+    if (fam == kFamInterleave) return check_state<kFamInterleave, MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+    return check_state<kFamPoseAll, MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
 }
 
 }  // namespace vp

@@ -177,4 +177,42 @@ int pack_env(const vp_env_desc *e, float4 *out, size_t cap_float4, EnvView *view
     return 0;
 }
 
+void reorder_env(const std::vector<float4> &in, const std::vector<unsigned> &hits, EnvView *view,
+                 std::vector<float4> *out) {
+    const int n[3] = {view->ns, view->nc, view->nb};
+    const int words[3] = {1, 2, 4};
+    int first[3], word0[3], box0[3];  // first primitive index, first data word, first box word of each kind
+    first[0] = 0;
+    first[1] = n[0];
+    first[2] = n[0] + n[1];
+    word0[0] = 0;
+    word0[1] = n[0];
+    word0[2] = n[0] + 2 * n[1];
+    const int data_words = n[0] + 2 * n[1] + 4 * n[2];
+    box0[0] = data_words;
+    box0[1] = data_words + 2 * n[0];
+    box0[2] = data_words + 2 * (n[0] + n[1]);
+    *out = in;
+    unsigned long long total[3] = {0, 0, 0};
+    for (int kind = 0; kind < 3; ++kind) {
+        std::vector<int> idx(static_cast<size_t>(n[kind]));
+        for (int k = 0; k < n[kind]; ++k) {
+            idx[k] = k;
+            total[kind] += hits[first[kind] + k];
+        }
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return hits[first[kind] + a] > hits[first[kind] + b]; });
+        for (int k = 0; k < n[kind]; ++k) {
+            const int src = idx[k];
+            for (int w = 0; w < words[kind]; ++w)
+                (*out)[word0[kind] + k * words[kind] + w] = in[word0[kind] + src * words[kind] + w];
+            for (int w = 0; w < 2; ++w) (*out)[box0[kind] + 2 * k + w] = in[box0[kind] + 2 * src + w];
+        }
+    }
+    // kinds by their total hits (ties keep the previous order)
+    int kinds[3] = {view->kind_order & 15, (view->kind_order >> 4) & 15, (view->kind_order >> 8) & 15};
+    std::stable_sort(kinds, kinds + 3, [&](int a, int b) { return total[a] > total[b]; });
+    view->kind_order = kinds[0] | (kinds[1] << 4) | (kinds[2] << 8);
+}
+
 }  // namespace vp

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "vp_types.h"
 
@@ -35,8 +36,10 @@ inline int lmax_for(int n_links) { return n_links <= 8 ? 8 : n_links <= 9 ? 9 : 
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st);
+// Sets the shared-memory attribute of every family's instance; the
+// occupancy returned is that of the family of check order `order`.
 cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, bool staged, size_t smem, int block,
-                                int *blocks_per_sm);
+                                int *blocks_per_sm, int order);
 
 cudaError_t launch_states(const RobotParams &P, const EnvView &env, const float *q, int64_t N, uint8_t *valid,
                           unsigned *status, int grid, int block, size_t smem, cudaStream_t st);
@@ -49,6 +52,26 @@ int fk_configs_per_block(int n_spheres);
 
 cudaError_t launch_counts(int D, const float *q0, const float *q1, float res, int64_t E, int32_t *counts,
                           cudaStream_t st);
+
+// The frequent-first order of the self-pair groups: how often each group
+// collides over configurations q [N][D] (device), most often first (ties in
+// packed order) into order[kMaxGroups], and into *n_front the number of
+// leading groups checked before the primitives (those that together hold
+// three quarters of the collisions counted).  Synchronises st.  0 = ok,
+// 2 = CUDA error (message in *msg).
+int group_order(const RobotParams &P, const float *q, int64_t N, cudaStream_t st, uint8_t *order, int *n_front,
+                std::string *msg);
+
+// How often each packed primitive (spheres, capsules, cuboids, in packed
+// order) touches a robot sphere over configurations q [N][D] (device).
+// Synchronises st.  0 = ok, 2 = CUDA error.
+int prim_hits(const RobotParams &P, const EnvView &env, const float *q, int64_t N, cudaStream_t st,
+              std::vector<unsigned> *hits, std::string *msg);
+// The packed environment `in` with each kind's primitives (and their world
+// boxes) reordered most often hit first (ties keep their order), and the
+// kinds visited in order of their total hits; *view gets the new kind order.
+void reorder_env(const std::vector<float4> &in, const std::vector<unsigned> &hits, EnvView *view,
+                 std::vector<float4> *out);
 
 // Batched randomized shortcutting (vp_shortcut.cu): the propose and apply
 // steps of one iteration.

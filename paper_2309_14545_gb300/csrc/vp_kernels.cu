@@ -2,6 +2,10 @@
 // states), state validation, FK sphere centres and edge state counts.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "vp_validate.cuh"
 
 namespace vp {
@@ -117,6 +121,86 @@ __global__ void counts_kernel(const int D, const float *__restrict__ q0, const f
     counts[e] = fin ? count_from_dmax(dmax, res) : -1;
 }
 
+// How often each self-pair group (link pair) collides: one configuration
+// per thread, every link frame kept (in local memory), every group's sphere
+// pairs tested until one collides; hits[g] counts the configurations in
+// which group g has a colliding pair.  Feeds the frequent-first check order.
+__global__ void group_hits_kernel(const __grid_constant__ RobotParams P, const float *__restrict__ q,
+                                  const long long N, unsigned *__restrict__ hits) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int D = P.n_joints;
+    const float *qi = q + i * D;
+    for (int j = 0; j < D; ++j)
+        if (!isfinite(qi[j])) return;
+    Fr F[kMaxLinks];
+    fr_identity(F[0]);
+    for (int j = 0; j < D; ++j) {
+        const JointC &J = P.joints[j];
+        F[j + 1] = F[(J.meta >> kMetaParentLinkShift) & 0xFF];
+        apply_joint(J, qi[j], F[j + 1]);
+    }
+    for (int g = 0; g < P.n_groups; ++g) {
+        const GroupC G = P.groups[g];
+        bool hit = false;
+        for (int p = G.p0; p < G.p1 && !hit; ++p) {
+            const PairC pr = P.pairs[p];
+            const float4 sa = P.spheres[pr.a], sb = P.spheres[pr.b];
+            const float3 a = fr_apply(F[G.la], sa.x, sa.y, sa.z);
+            const float3 b = fr_apply(F[G.lb], sb.x, sb.y, sb.z);
+            const float ex = a.x - b.x, ey = a.y - b.y, ez = a.z - b.z;
+            const float r2 = sa.w + sb.w;
+            hit = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2;
+        }
+        if (hit) atomicAdd(&hits[g], 1u);
+    }
+}
+
+// How often each primitive collides: one configuration per thread, every
+// link frame kept; for every primitive (packed order, kinds one after the
+// other), each link's bounding sphere is tested and, where it touches, the
+// link's spheres; hits[k] counts the configurations in which primitive k
+// touches some sphere.  Feeds the environment's visiting order.
+template <int KIND>
+__device__ __forceinline__ void count_kind(const RobotParams &P, const Fr *F, const float4 *prims, int n,
+                                           unsigned *hits) {
+    using K = Kind<KIND>;
+    for (int k = 0; k < n; ++k) {
+        const float4 *o = prims + k * K::kWords;
+        bool hit = false;
+        for (int l = 0; l < P.n_links && !hit; ++l) {
+            const LinkC &L = P.links[l];
+            if (L.s0 >= L.s1 || !K::hit(fr_apply(F[l], L.bs.x, L.bs.y, L.bs.z), L.bs.w, o)) continue;
+            for (int sp = L.s0; sp < L.s1 && !hit; ++sp) {
+                const float4 c = P.spheres[sp];
+                hit = K::hit(fr_apply(F[l], c.x, c.y, c.z), c.w, o);
+            }
+        }
+        if (hit) atomicAdd(&hits[k], 1u);
+    }
+}
+
+__global__ void prim_hits_kernel(const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q,
+                                 const long long N, unsigned *__restrict__ hits) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int D = P.n_joints;
+    const float *qi = q + i * D;
+    for (int j = 0; j < D; ++j)
+        if (!isfinite(qi[j])) return;
+    Fr F[kMaxLinks];
+    fr_identity(F[0]);
+    for (int j = 0; j < D; ++j) {
+        const JointC &J = P.joints[j];
+        F[j + 1] = F[(J.meta >> kMetaParentLinkShift) & 0xFF];
+        apply_joint(J, qi[j], F[j + 1]);
+    }
+    const EnvSm e = env_views<false>(nullptr, env);
+    count_kind<0>(P, F, e.sph, e.ns, hits);
+    count_kind<1>(P, F, e.cap, e.nc, hits + e.ns);
+    count_kind<2>(P, F, e.box, e.nb, hits + e.ns + e.nc);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 
@@ -127,16 +211,44 @@ static cudaError_t prepare(K kernel, size_t smem, int block, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, block, smem);
 }
 
+const KernelSet &kernel_set(int lmax) {
+    auto make = [](void (*f0)(KernelSet &), void (*f1)(KernelSet &), void (*f2)(KernelSet &)) {
+        KernelSet s;
+        f0(s);
+        f1(s);
+        f2(s);
+        return s;
+    };
+    static const KernelSet s8 = make(kernel_set_fill_l8_f0, kernel_set_fill_l8_f1, kernel_set_fill_l8_f2);
+    static const KernelSet s9 = make(kernel_set_fill_l9_f0, kernel_set_fill_l9_f1, kernel_set_fill_l9_f2);
+    static const KernelSet s15 = make(kernel_set_fill_l15_f0, kernel_set_fill_l15_f1, kernel_set_fill_l15_f2);
+    static const KernelSet s17 = make(kernel_set_fill_l17_f0, kernel_set_fill_l17_f1, kernel_set_fill_l17_f2);
+    switch (lmax) {
+        case 8: return s8;
+        case 9: return s9;
+        case 15: return s15;
+        default: return s17;
+    }
+}
+
 cudaError_t prepare_edges_plain(bool stats, int lmax, bool simple, bool staged, size_t smem, int block,
-                                int *blocks_per_sm) {
-    return prepare(kernel_set(lmax).plain[stats][simple][staged], smem, block, blocks_per_sm);
+                                int *blocks_per_sm, int order) {
+    // every family's attribute is set; the occupancy is that of the family of `order`
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < kFamCount && e == cudaSuccess; ++f)
+        if (f != family_of(order))
+            e = cudaFuncSetAttribute(kernel_set(lmax).plain[f][stats][simple][staged],
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return prepare(kernel_set(lmax).plain[family_of(order)][stats][simple][staged], smem, block, blocks_per_sm);
 }
 
 cudaError_t launch_edges_plain(const RobotParams &P, const EnvView &env, const float *q0, const float *q1,
                                const int32_t *counts, float res, int64_t E, uint8_t *valid, unsigned *status,
                                unsigned long long *work, int grid, int block, size_t smem, cudaStream_t st) {
-    kernel_set(lmax_for(P.n_links)).plain[work != nullptr][P.simple != 0][env.staged != 0]<<<grid, block, smem, st>>>(
-        P, env, q0, q1, counts, res, E, valid, status, work);
+    kernel_set(lmax_for(P.n_links))
+        .plain[family_of(env.order)][work != nullptr][P.simple != 0][env.staged != 0]<<<grid, block, smem, st>>>(
+            P, env, q0, q1, counts, res, E, valid, status, work);
     return cudaGetLastError();
 }
 
@@ -177,6 +289,74 @@ cudaError_t launch_fk(const RobotParams &P, const float *q, int64_t N, float *ce
                       size_t smem, cudaStream_t st) {
     fk_kernel<<<grid, block, smem, st>>>(P, q, N, centres);
     return cudaGetLastError();
+}
+
+int group_order(const RobotParams &P, const float *q, int64_t N, cudaStream_t st, uint8_t *order, int *n_front,
+                std::string *msg) {
+    const int ng = P.n_groups;
+    for (int g = 0; g < kMaxGroups; ++g) order[g] = static_cast<uint8_t>(g < ng ? g : 0);
+    *n_front = ng;
+    if (ng == 0 || N <= 0) return 0;
+    unsigned *d_hits = nullptr;
+    std::vector<unsigned> hits(static_cast<size_t>(ng), 0u);
+    cudaError_t e = cudaMalloc(&d_hits, sizeof(unsigned) * ng);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hits, 0, sizeof(unsigned) * ng, st);
+    if (e == cudaSuccess) {
+        const int block = 128;
+        group_hits_kernel<<<static_cast<unsigned>((N + block - 1) / block), block, 0, st>>>(P, q, N, d_hits);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hits.data(), d_hits, sizeof(unsigned) * ng, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_hits) cudaFree(d_hits);
+    if (e != cudaSuccess) {
+        *msg = std::string("group hit count: ") + cudaGetErrorString(e);
+        return 2;
+    }
+    std::vector<int> idx(static_cast<size_t>(ng));
+    for (int g = 0; g < ng; ++g) idx[g] = g;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return hits[a] > hits[b]; });
+    for (int g = 0; g < ng; ++g) order[g] = static_cast<uint8_t>(idx[g]);
+    // the leading groups that hold three quarters of the counted collisions
+    // go before the primitives (all of them when nothing collided)
+    unsigned long long total = 0, run = 0;
+    for (int g = 0; g < ng; ++g) total += hits[g];
+    int front = ng;
+    if (total > 0)
+        for (int g = 0; g < ng; ++g) {
+            run += hits[idx[g]];
+            if (4 * run >= 3 * total) {
+                front = g + 1;
+                break;
+            }
+        }
+    *n_front = front;
+    return 0;
+}
+
+int prim_hits(const RobotParams &P, const EnvView &env, const float *q, int64_t N, cudaStream_t st,
+              std::vector<unsigned> *hits, std::string *msg) {
+    const int n = env.ns + env.nc + env.nb;
+    hits->assign(static_cast<size_t>(n), 0u);
+    if (n == 0 || N <= 0) return 0;
+    unsigned *d_hits = nullptr;
+    cudaError_t e = cudaMalloc(&d_hits, sizeof(unsigned) * n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hits, 0, sizeof(unsigned) * n, st);
+    if (e == cudaSuccess) {
+        EnvView v = env;
+        v.staged = 0;
+        const int block = 128;
+        prim_hits_kernel<<<static_cast<unsigned>((N + block - 1) / block), block, 0, st>>>(P, v, q, N, d_hits);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hits->data(), d_hits, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_hits) cudaFree(d_hits);
+    if (e != cudaSuccess) {
+        *msg = std::string("primitive hit count: ") + cudaGetErrorString(e);
+        return 2;
+    }
+    return 0;
 }
 
 cudaError_t launch_counts(int D, const float *q0, const float *q1, float res, int64_t E, int32_t *counts,

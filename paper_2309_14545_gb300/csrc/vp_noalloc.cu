@@ -157,7 +157,8 @@ extern "C" vp_status vp_validate_edges_noalloc(const vp_robot_desc *robot, const
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int bps = 0;
-    e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, ev.staged != 0, smem, block, &bps);
+    e = prepare_edges_plain(false, lmax_for(rp.n_links), rp.simple != 0, ev.staged != 0, smem, block, &bps,
+                            ev.order);
     if (e == cudaSuccess && bps < 1) {  // the same status the context path reports
         set_msg(errbuf, errbuf_len, "plain edge kernel cannot be resident");
         return VP_ERR_CAPACITY;

@@ -162,7 +162,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5)
                         if (i >= k) i = k - 1;
                         const float tt = static_cast<float>(i) * inv;
                         const WorkRef<false> w{nullptr, false};
-                        const bool c = pose_and_check<kStopAny, false, LMAX, SIMPLE>(
+                        const bool c = check_state<kFamPoseAll, kStopAny, false, LMAX, SIMPLE>(
                             P, [tt, wq0, wdq](int j) { return fmaf(tt, wdq[j], wq0[j]); }, es, stash,
                             Ctl{kFull, false}, w);
                         if (__any_sync(kFull, c)) {

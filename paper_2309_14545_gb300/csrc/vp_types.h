@@ -71,6 +71,7 @@ struct RobotParams {
     int n_slots;    // frame-stash slots (branch points)
     unsigned link_mask;  // bit l: link l has spheres
     int simple;          // 1: canonical axes and identity origin rotations only
+    int n_gfront;        // frequent-first order: groups gorder[0, n_gfront) go before the primitives
     JointC joints[kMaxJoints];
     LinkC links[kMaxLinks];
     float4 halves[kMaxLinks][2];  // bounding spheres of a split link's halves (link frame, radius + eps)
@@ -78,6 +79,8 @@ struct RobotParams {
     GroupC groups[kMaxGroups];
     PairC pairs[kMaxPairs];
     uint16_t perm[kMaxSpheres];   // sorted index -> caller's sphere index
+    uint8_t gorder[kMaxGroups];   // the groups in the frequent-first order (kOrderFrequent):
+                                  // most often colliding first, as counted on a sample
 };
 
 // Environment layout (float4 units): spheres [ns] (c, r); capsules [2 nc]
@@ -97,13 +100,16 @@ struct EnvView {
     int order;       // check order (kOrder* bits, set per launch)
 };
 
-// Check order bits (EnvView::order): primitives before self pairs, and
-// checks interleaved with posing (each link checked as soon as it is posed,
-// later links left unposed once the state has collided) instead of every
-// link posed first.
+// Check orders (EnvView::order): 0-3 combine two bits, primitives before
+// self pairs and checks interleaved with posing (each link checked as soon
+// as it is posed, later links left unposed once the state has collided)
+// instead of every link posed first; 4 is the frequent-first order.
 constexpr int kOrderPrimsFirst = VP_ORDER_PRIMS_FIRST;
 constexpr int kOrderInterleave = VP_ORDER_INTERLEAVE;
-constexpr int kOrderCount = 4;
+// Self-pair groups most often colliding first (RobotParams::gorder), each
+// link posed when a check first needs it, then primitives.
+constexpr int kOrderFrequent = VP_ORDER_FREQUENT;
+constexpr int kOrderCount = 5;
 
 // Dynamic shared memory the environment takes in a block.
 __host__ __device__ inline size_t env_smem_bytes(const EnvView &env) {

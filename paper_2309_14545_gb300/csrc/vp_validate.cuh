@@ -1,10 +1,10 @@
 // Validation kernel templates: the plain edge kernel (one warp per edge),
 // the batched screening kernel and its second phase.  Each is instantiated
-// per link bound LMAX in its own translation unit (vp_inst_l*.cu), for the
-// counting mode STATS, the joint code SIMPLE and the environment placement
-// STAGED (copied into shared memory, or read in place through L1; the host
-// launches the instance matching EnvView::staged and sizes shared memory to
-// match).
+// per link bound LMAX and family of check orders FAM in its own translation
+// unit (vp_inst.cu, compiled once per pair), for the counting mode STATS,
+// the joint code SIMPLE and the environment placement STAGED (copied into
+// shared memory, or read in place through L1; the host launches the
+// instance matching EnvView::staged and sizes shared memory to match).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,7 +83,7 @@ __device__ __forceinline__ void flush_work(Work &wk, unsigned long long *work, i
 // One warp per edge.  Lane j of the warp checks states j*R + r in round r
 // (R = ceil(k/32) rounds): the rake of Sec. III-D, 32 spread states per
 // round.  Lanes past the end park on the last state.
-template <bool STATS, int LMAX, bool SIMPLE, bool STAGED>
+template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
 __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_constant__ RobotParams P, const EnvView env,
                                                           const float *__restrict__ q0, const float *__restrict__ q1,
                                                           const int32_t *__restrict__ counts, const float res,
@@ -147,7 +147,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_co
                 if (!real) i = k - 1;
                 const float t = static_cast<float>(i) * inv;
                 const WorkRef<STATS> w{&wk, real};
-                const bool c = pose_and_check<kStopAny, STATS, LMAX, SIMPLE>(
+                const bool c = check_state<FAM, kStopAny, STATS, LMAX, SIMPLE>(
                     P, [t, wq0, wdq](int j) { return fmaf(t, wdq[j], wq0[j]); }, es, stash, Ctl{kFull, false}, w);
                 if (__any_sync(kFull, c)) {
                     collided = true;
@@ -166,7 +166,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_co
 
 // Persistent validation of bucketed edges; see the file comment.  STATS adds
 // the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
-template <bool STATS, int LMAX, bool SIMPLE, bool STAGED>
+template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
 __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
     const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
@@ -282,7 +282,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
             const WorkRef<STATS> w{&wk, !done && i < k};
             if (i >= k) i = k - 1;
             const float t = static_cast<float>(i) * inv;
-            const bool c = pose_and_check<kStopGroups, STATS, LMAX, SIMPLE>(
+            const bool c = check_state<FAM, kStopGroups, STATS, LMAX, SIMPLE>(
                 P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w);
             const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
             if (!done && (gcol || r == R - 1)) {
@@ -319,7 +319,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
 // is spread over many warps instead of holding one lane group for all its
 // rounds.  A collision clears the edge's verdict; items of an edge already
 // found colliding are skipped.
-template <bool STATS, int LMAX, bool SIMPLE, bool STAGED>
+template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
 __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) survivors_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
     const float *__restrict__ q1, const int2 *__restrict__ surv, const BatchPlan plan, uint8_t *valid,
@@ -382,7 +382,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) survivors_kernel(
             const WorkRef<STATS> w{&wk, i < k};
             if (i >= k) i = k - 1;
             const float t = static_cast<float>(i) * inv;
-            const bool col = pose_and_check<kStopAny, STATS, LMAX, SIMPLE>(
+            const bool col = check_state<FAM, kStopAny, STATS, LMAX, SIMPLE>(
                 P, [t, wq0, wdq](int jj) { return fmaf(t, wdq[jj], wq0[jj]); }, es, stash, Ctl{kFull, false}, w);
             if (__any_sync(kFull, col)) {
                 if (lane == 0) vvalid[e] = 0;
@@ -400,30 +400,29 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) survivors_kernel(
     }
 }
 
-// Every instance of one link bound: [stats][simple][staged] (the counting
-// variant always takes the general joint code).
-template <int LMAX>
-KernelSet make_kernel_set() {
-    KernelSet s;
-    s.plain[0][0][0] = edges_plain_kernel<false, LMAX, false, false>;
-    s.plain[0][0][1] = edges_plain_kernel<false, LMAX, false, true>;
-    s.plain[0][1][0] = edges_plain_kernel<false, LMAX, true, false>;
-    s.plain[0][1][1] = edges_plain_kernel<false, LMAX, true, true>;
-    s.plain[1][0][0] = s.plain[1][1][0] = edges_plain_kernel<true, LMAX, false, false>;
-    s.plain[1][0][1] = s.plain[1][1][1] = edges_plain_kernel<true, LMAX, false, true>;
-    s.batched[0][0][0] = edges_batched_kernel<false, LMAX, false, false>;
-    s.batched[0][0][1] = edges_batched_kernel<false, LMAX, false, true>;
-    s.batched[0][1][0] = edges_batched_kernel<false, LMAX, true, false>;
-    s.batched[0][1][1] = edges_batched_kernel<false, LMAX, true, true>;
-    s.batched[1][0][0] = s.batched[1][1][0] = edges_batched_kernel<true, LMAX, false, false>;
-    s.batched[1][0][1] = s.batched[1][1][1] = edges_batched_kernel<true, LMAX, false, true>;
-    s.survivors[0][0][0] = survivors_kernel<false, LMAX, false, false>;
-    s.survivors[0][0][1] = survivors_kernel<false, LMAX, false, true>;
-    s.survivors[0][1][0] = survivors_kernel<false, LMAX, true, false>;
-    s.survivors[0][1][1] = survivors_kernel<false, LMAX, true, true>;
-    s.survivors[1][0][0] = s.survivors[1][1][0] = survivors_kernel<true, LMAX, false, false>;
-    s.survivors[1][0][1] = s.survivors[1][1][1] = survivors_kernel<true, LMAX, false, true>;
-    return s;
+// Every instance of one link bound and kernel family into s: [FAM][stats]
+// [simple][staged] (the counting variant always takes the general joint
+// code).
+template <int LMAX, int FAM>
+void fill_kernel_set(KernelSet &s) {
+    s.plain[FAM][0][0][0] = edges_plain_kernel<false, LMAX, false, false, FAM>;
+    s.plain[FAM][0][0][1] = edges_plain_kernel<false, LMAX, false, true, FAM>;
+    s.plain[FAM][0][1][0] = edges_plain_kernel<false, LMAX, true, false, FAM>;
+    s.plain[FAM][0][1][1] = edges_plain_kernel<false, LMAX, true, true, FAM>;
+    s.plain[FAM][1][0][0] = s.plain[FAM][1][1][0] = edges_plain_kernel<true, LMAX, false, false, FAM>;
+    s.plain[FAM][1][0][1] = s.plain[FAM][1][1][1] = edges_plain_kernel<true, LMAX, false, true, FAM>;
+    s.batched[FAM][0][0][0] = edges_batched_kernel<false, LMAX, false, false, FAM>;
+    s.batched[FAM][0][0][1] = edges_batched_kernel<false, LMAX, false, true, FAM>;
+    s.batched[FAM][0][1][0] = edges_batched_kernel<false, LMAX, true, false, FAM>;
+    s.batched[FAM][0][1][1] = edges_batched_kernel<false, LMAX, true, true, FAM>;
+    s.batched[FAM][1][0][0] = s.batched[FAM][1][1][0] = edges_batched_kernel<true, LMAX, false, false, FAM>;
+    s.batched[FAM][1][0][1] = s.batched[FAM][1][1][1] = edges_batched_kernel<true, LMAX, false, true, FAM>;
+    s.survivors[FAM][0][0][0] = survivors_kernel<false, LMAX, false, false, FAM>;
+    s.survivors[FAM][0][0][1] = survivors_kernel<false, LMAX, false, true, FAM>;
+    s.survivors[FAM][0][1][0] = survivors_kernel<false, LMAX, true, false, FAM>;
+    s.survivors[FAM][0][1][1] = survivors_kernel<false, LMAX, true, true, FAM>;
+    s.survivors[FAM][1][0][0] = s.survivors[FAM][1][1][0] = survivors_kernel<true, LMAX, false, false, FAM>;
+    s.survivors[FAM][1][0][1] = s.survivors[FAM][1][1][1] = survivors_kernel<true, LMAX, false, true, FAM>;
 }
 
 }  // namespace vp

@@ -164,11 +164,11 @@ def test_second_phase_matches_plain(vpmod, name, n):
             val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
             assert np.array_equal(out.cpu().numpy(), want), (rounds, lanes)
     # the other check orders (primitives first; checks interleaved with
-    # posing, either way round): the same verdicts in both modes, and for
-    # states
+    # posing, either way round; frequent link pairs first with links posed
+    # on demand): the same verdicts in both modes, and for states
     states = q0[: min(n, 20000)]
     want_s = val.validate_states(states).cpu().numpy()
-    for order in (1, 2, 3):
+    for order in (1, 2, 3, 4):
         val.set_check_order(order)
         assert val.check_order() == order
         for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
@@ -182,9 +182,16 @@ def test_second_phase_matches_plain(vpmod, name, n):
     assert val.sync_status()[0] == vp.VP_OK
     with pytest.raises(vp.VPError):
         val.set_screen_rounds(-1)
-    for bad in (-1, 4):
+    for bad in (-1, 5):
         with pytest.raises(vp.VPError):
             val.set_check_order(bad)
+    # the frequent-first order after the tuner has counted the groups
+    val.autotune(q0, q1, c, float(w.res))
+    val.set_check_order(4)
+    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
+        got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
+        assert np.array_equal(got, want), ("tuned 4", mode)
+    assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s)
     val.close()
 
 
