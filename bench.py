@@ -658,16 +658,26 @@ def shortcut_leg(dev, flush, stream):
 def rrt_leg(dev, flush, stream):
     """Batched RRT-Connect: 4,096 problems of the 7-DoF arm among 16
     spheres and 2,048 of the torso arm among 80 obstacles, 1,024 samples
-    each; one warp per problem, trees on the device."""
+    each; one warp per problem, trees on the device.  Start and goal are
+    drawn from collision-free configurations: candidates uniform in the
+    limits, kept where the GPU's state check finds them valid (the
+    rejection rate is reported), the first B valid ones as starts and the
+    next B as goals."""
     import torch
     from paper_2309_14545_gb300 import Validator
     out = {}
     for name, B, T, rng, cap in vpgen.RRT_CASES:
         w = vpgen.workload(name, n_edges=16)
-        v = Validator(w.robot, w.env, device=dev.index)
-        start, goal, samples = vpgen.rrt_problems(w.robot, B, T, seed=vpgen.RRT_SEED)
+        v = Validator(w.robot, w.env)
+        _, _, samples = vpgen.rrt_problems(w.robot, B, T, seed=vpgen.RRT_SEED)
+        cand = vpgen.uniform_configs(w.robot, 8 * B, seed=vpgen.RRT_SEED + 1)
         with torch.cuda.stream(stream):
-            s, g, q = (torch.from_numpy(x).to(dev) for x in (start, goal, samples))
+            ok = v.validate_states(torch.from_numpy(cand).to(dev), stream=stream).cpu().numpy().astype(bool)
+        pool = cand[ok]
+        nb = min(B, pool.shape[0] // 2)
+        start, goal = pool[:nb], pool[nb:2 * nb]
+        with torch.cuda.stream(stream):
+            s, g, q = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (start, goal, samples[:nb]))
         res = {}
 
         def run():
@@ -676,11 +686,13 @@ def rrt_leg(dev, flush, stream):
         med, mn = _timed(run, flush, stream, 3)
         st = res["status"].cpu().numpy()
         solved = st == 1
-        out[name] = {"problems": B, "samples": T, "range": rng, "cap": cap, "ms": med,
-                     "problems_per_s": B / (med / 1e3), "solved": float(solved.mean()),
+        out[name] = {"problems": nb, "samples": T, "range": rng, "cap": cap, "ms": med,
+                     "problems_per_s": nb / (med / 1e3), "solved": float(solved.mean()),
+                     "endpoint_rejection_rate": float(1.0 - ok.mean()),
                      "invalid_endpoints": float((st == -1).mean()),
                      "mean_samples_used_solved": float(res["iters"].cpu().numpy()[solved].mean()) if solved.any()
                      else None,
+                     "max_samples_used": int(res["iters"].cpu().numpy().max()),
                      "mean_path_waypoints": float(res["path_len"].cpu().numpy()[solved].mean()) if solved.any()
                      else None}
         v.close()
@@ -708,8 +720,9 @@ def fk_leg(dev, flush, stream):
             c = torch.empty((N, S, 3), dtype=torch.float32, device=dev)
         rec = {"configs": N, "spheres": S, "bytes": N * (D + 3 * S) * 4}
         for tag, gen in (("table", False), ("generated", True)):
+            t = v.fk_codegen(gen)  # pin the kernel (the default would generate it)
             if gen:
-                rec["compile_ms"] = v.fk_codegen(True)
+                rec["compile_ms"] = t
             med, mn = _timed(lambda: vp.vp_fk_spheres(v.ctx, q, c, stream), flush, stream, 5)
             gbs = rec["bytes"] / (med / 1e3) / 1e9
             rec[tag] = {"ms": med, "configs_per_s": N / (med / 1e3),

@@ -152,9 +152,12 @@ vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *robot);
  * Synchronous.  VP_ERR_CAPACITY if it packs to more than VP_MAX_ENV_BYTES. */
 vp_status vp_load_env(vp_ctx *ctx, const vp_env_desc *env);
 
-/* FK test hook (Sec. III-B): world sphere centres of n configurations.
- * q: device float [n][D]; centres: device float [n][S][3], spheres in the
- * robot's original order. */
+/* FK (Sec. III-B): world sphere centres of n configurations.  q: device
+ * float [n][D]; centres: device float [n][S][3], spheres in the robot's
+ * original order.  By default the first call after a robot load generates
+ * and compiles that robot's FK kernel (vp_fk_codegen; tens of ms, on the
+ * host) and uses it from then on; where that fails (no NVRTC) the
+ * table-driven kernel serves instead.  vp_fk_codegen pins either. */
 vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float *centres, void *stream);
 
 /* State validity (Sec. III-C): valid[i] = 1 iff configuration i collides with
@@ -342,15 +345,18 @@ vp_status vp_shortcut_paths(vp_ctx *ctx, float *paths, int32_t *lengths, int64_t
 
 /* Per-robot forward kinematics by code generation (Sec. III-B: the paper's
  * tracing compiler turns the robot's kinematics into straight-line code with
- * its constants folded in).  enable != 0: generate a CUDA kernel for the
+ * its constants folded in).  enable == 1: generate a CUDA kernel for the
  * loaded robot (every joint and sphere unrolled, fixed transforms and sphere
  * offsets as literals, zero terms dropped), compile it with NVRTC for the
  * current device (the first time), and make vp_fk_spheres use it; it
  * computes what the table-driven kernel computes, in the same order of
- * operations.  enable == 0: back to the table-driven kernel.  Loading a
- * robot drops the generated kernel.  *compile_ms (may be NULL) gets the
- * generation and compile time.  VP_ERR_CUDA (and the table-driven kernel
- * stays in use) when NVRTC is missing or compilation fails. */
+ * operations.  enable == 0: the table-driven kernel.  enable == -1: the
+ * default after every robot load -- the generated kernel, built on the
+ * first vp_fk_spheres call, or the table-driven one where building fails.
+ * Loading a robot drops the generated kernel.  *compile_ms (may be NULL)
+ * gets the generation and compile time (0 if none was built).  VP_ERR_CUDA
+ * (and the previous choice stays in use) when enable == 1 and NVRTC is
+ * missing or compilation fails; VP_ERR_ARG for another value of enable. */
 vp_status vp_fk_codegen(vp_ctx *ctx, int enable, double *compile_ms);
 
 /* Batched RRT-Connect (Sec. III-E, "Bringing it Together": RRT-Connect is one

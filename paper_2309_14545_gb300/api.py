@@ -126,9 +126,11 @@ class Validator:
         return out
 
     def fk_codegen(self, enable=True):
-        """Use (or stop using) the per-robot FK kernel generated and compiled
-        at run time for fk_spheres; returns the compile time in ms."""
-        return vp.vp_fk_codegen(self.ctx, enable)
+        """The FK kernel fk_spheres uses: True (1) the per-robot kernel
+        generated and compiled at run time, False (0) the table-driven one,
+        -1 automatic (the default: generated, else the table); returns the
+        compile time in ms."""
+        return vp.vp_fk_codegen(self.ctx, int(enable))
 
     def nearest(self, points, queries, stream=None):
         """(index int64 [N], squared distance float32 [N]) of each query's

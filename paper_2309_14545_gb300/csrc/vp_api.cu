@@ -44,7 +44,8 @@ struct vp_ctx {
     int *rrt_parent = nullptr, *rrt_queue = nullptr;
     size_t rrt_node_cap = 0, rrt_parent_cap = 0;
     FkCodegen fk_gen;            // per-robot FK compiled at run time (vp_fk_codegen)
-    bool fk_gen_on = false;
+    int fk_mode = -1;            // 1 generated, 0 table-driven, -1 automatic (generated once it builds)
+    bool fk_gen_failed = false;  // automatic mode: the generator failed for this robot (use the table)
     std::string err;
 };
 
@@ -466,7 +467,8 @@ extern "C" vp_status vp_load_robot(vp_ctx *ctx, const vp_robot_desc *r) {
         DeviceGuard g(ctx->device);
         fk_codegen_release(&ctx->fk_gen);
     }
-    ctx->fk_gen_on = false;
+    ctx->fk_mode = -1;
+    ctx->fk_gen_failed = false;
     return VP_OK;
 }
 
@@ -562,7 +564,13 @@ extern "C" vp_status vp_fk_spheres(vp_ctx *ctx, const float *q, int64_t n, float
     if (n == 0) return VP_OK;
     if (!q || !centres) return fail(ctx, VP_ERR_ARG, "NULL buffer");
     DeviceGuard g(ctx->device);
-    if (ctx->fk_gen_on) {
+    if (ctx->fk_mode == -1 && !ctx->fk_gen.kernel && !ctx->fk_gen_failed) {
+        // automatic: generate and compile the robot's FK on first use; if
+        // that fails (no NVRTC), the table-driven kernel serves from now on
+        std::string msg;
+        ctx->fk_gen_failed = fk_codegen_build(ctx->robot, &ctx->fk_gen, &msg) != 0;
+    }
+    if (ctx->fk_mode == 1 || (ctx->fk_mode == -1 && ctx->fk_gen.kernel)) {
         const cudaError_t e =
             fk_codegen_launch(ctx->fk_gen, ctx->robot.n_spheres, q, n, centres, static_cast<cudaStream_t>(stream));
         return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_fk_spheres (generated)");
@@ -959,15 +967,17 @@ extern "C" vp_status vp_fk_codegen(vp_ctx *ctx, int enable, double *compile_ms) 
     if (!ctx) return VP_ERR_ARG;
     if (!ctx->robot_loaded) return fail(ctx, VP_ERR_NOT_LOADED, "robot not loaded");
     DeviceGuard g(ctx->device);
-    if (!enable) {
-        ctx->fk_gen_on = false;
+    if (enable < -1 || enable > 1) return fail(ctx, VP_ERR_ARG, "vp_fk_codegen: enable must be -1, 0 or 1");
+    if (enable != 1) {
+        ctx->fk_mode = enable;
+        if (compile_ms) *compile_ms = ctx->fk_gen.kernel ? ctx->fk_gen.compile_ms : 0.0;
         return VP_OK;
     }
     if (!ctx->fk_gen.kernel) {
         std::string msg;
         if (fk_codegen_build(ctx->robot, &ctx->fk_gen, &msg) != 0) return fail(ctx, VP_ERR_CUDA, "vp_fk_codegen: %s", msg.c_str());
     }
-    ctx->fk_gen_on = true;
+    ctx->fk_mode = 1;
     if (compile_ms) *compile_ms = ctx->fk_gen.compile_ms;
     return VP_OK;
 }

@@ -333,10 +333,11 @@ def vp_rrt_connect(ctx, start, goal, samples, range_, resolution, cap, status, i
 
 
 def vp_fk_codegen(ctx, enable=True):
-    """Switch vp_fk_spheres to (or from) the per-robot generated kernel;
-    returns the generation and compile time in ms."""
+    """Choose vp_fk_spheres' kernel: 1 (True) the per-robot generated one,
+    0 (False) the table-driven one, -1 automatic; returns the generation and
+    compile time in ms."""
     ms = C.c_double(0.0)
-    _check(ctx, lib.vp_fk_codegen(ctx, int(bool(enable)), C.byref(ms)))
+    _check(ctx, lib.vp_fk_codegen(ctx, int(enable), C.byref(ms)))
     return ms.value
 
 

@@ -39,13 +39,20 @@ def test_generated_fk_matches_table_and_oracle(vpmod, make):
     r = make()
     val = Validator(r, EMPTY_ENV)
     q = torch.from_numpy(vpgen.uniform_configs(r, 4099, seed=8)).cuda()
+    default = val.fk_spheres(q).cpu().numpy()  # the automatic choice: the generated kernel
+    val.fk_codegen(False)
     table = val.fk_spheres(q).cpu().numpy()
     ms = val.fk_codegen(True)
     assert ms > 0
     gen = val.fk_spheres(q).cpu().numpy()
+    assert np.array_equal(gen, default)
     val.fk_codegen(False)
     again = val.fk_spheres(q).cpu().numpy()
     assert np.array_equal(again, table)  # switched back to the table
+    val.fk_codegen(-1)
+    assert np.array_equal(val.fk_spheres(q).cpu().numpy(), gen)
+    with pytest.raises(vp.VPError):
+        val.fk_codegen(2)
     assert np.abs(gen - table).max() <= 4e-7 * max(1.0, np.abs(table).max())
     want = oracle.Oracle(r, EMPTY_ENV).fk(q.cpu().numpy().astype(np.float64))
     assert np.abs(gen - want).max() < 1e-5
