@@ -41,8 +41,9 @@ struct vp_ctx {
     int sc_dof = 0;
     // planner scratch: tree nodes and parents, and the problem counter
     float *rrt_nodes = nullptr;
-    int *rrt_parent = nullptr, *rrt_queue = nullptr;
-    size_t rrt_node_cap = 0, rrt_parent_cap = 0;
+    int *rrt_parent = nullptr, *rrt_queue = nullptr;  // rrt_queue: 3 counters
+    int *rrt_pending = nullptr;                        // [B] ints, then [B] int4 (saved states)
+    size_t rrt_node_cap = 0, rrt_parent_cap = 0, rrt_pending_cap = 0;
     FkCodegen fk_gen;            // per-robot FK compiled at run time (vp_fk_codegen)
     int fk_mode = -1;            // 1 generated, 0 table-driven, -1 automatic (generated once it builds)
     bool fk_gen_failed = false;  // automatic mode: the generator failed for this robot (use the table)
@@ -142,6 +143,7 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->rrt_nodes) cudaFree(ctx->rrt_nodes);
         if (ctx->rrt_parent) cudaFree(ctx->rrt_parent);
         if (ctx->rrt_queue) cudaFree(ctx->rrt_queue);
+        if (ctx->rrt_pending) cudaFree(ctx->rrt_pending);
         fk_codegen_release(&ctx->fk_gen);
     }
     delete ctx;
@@ -948,13 +950,28 @@ extern "C" vp_status vp_rrt_connect(vp_ctx *ctx, const float *start, const float
         ctx->rrt_node_cap = ctx->rrt_parent_cap = 0;
         e = cudaMalloc(&ctx->rrt_nodes, n_nodes * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&ctx->rrt_parent, n_par * sizeof(int));
-        if (e == cudaSuccess && !ctx->rrt_queue) e = cudaMalloc(&ctx->rrt_queue, sizeof(int));
+        if (e == cudaSuccess && !ctx->rrt_queue) e = cudaMalloc(&ctx->rrt_queue, 3 * sizeof(int));
         if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_rrt_connect (scratch)");
         ctx->rrt_node_cap = n_nodes;
         ctx->rrt_parent_cap = n_par;
     }
+    // problems the first phase sets aside: their indices, then where each stands
+    const size_t n_idx = ((static_cast<size_t>(B) + 3) / 4) * 4;  // B indices, padded to 16 bytes
+    const size_t n_pend = n_idx + static_cast<size_t>(B) * 4;      // then B int4
+    if (n_pend > ctx->rrt_pending_cap) {
+        cudaStreamSynchronize(st);
+        cudaFree(ctx->rrt_pending);
+        ctx->rrt_pending = nullptr;
+        ctx->rrt_pending_cap = 0;
+        e = cudaMalloc(&ctx->rrt_pending, n_pend * sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_rrt_connect (scratch)");
+        ctx->rrt_pending_cap = n_pend;
+    }
+    // the int4 array starts at the first 16-byte boundary after the B indices
+    int *save_base = ctx->rrt_pending + n_idx;
     RRTLaunch L{start, goal, samples, B, T, cap, range, resolution, ctx->rrt_nodes, ctx->rrt_parent, ctx->rrt_queue,
-                status, iters, path, path_len, tree_sizes, ctx->batched.watchdog_ns};
+                ctx->rrt_pending, reinterpret_cast<int4 *>(save_base), status, iters, path, path_len, tree_sizes,
+                ctx->batched.watchdog_ns};
     EnvView view = ctx->env;
     view.order = batched_check_order(ctx->batched);
     std::string msg;

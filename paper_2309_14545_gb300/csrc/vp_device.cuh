@@ -493,6 +493,16 @@ __device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const S
     return b;
 }
 
+// A team of warps checking the same states together (the RRT-Connect
+// kernel's second phase): warp `part` of `nparts` takes every nparts-th
+// self-pair group and primitive batch, and a warp that finds a collision
+// raises `flag` (shared memory) so that the others stop at their next group
+// or batch.  The default (nparts == 1) is a warp checking everything.
+struct Team {
+    int part = 0, nparts = 1;
+    volatile int *flag = nullptr;
+};
+
 // Every primitive of one kind (largest first) against every link's bounding
 // sphere, then the fine spheres of each link some lane's coarse test hit.
 // Primitives go in batches of 32 / LMAX: lane t compares the world box of
@@ -501,18 +511,20 @@ __device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const S
 // take the exact ball test.  The cull is conservative (the primitive boxes
 // carry a rounding margin), so the verdicts are those of testing every pair.
 // Returns the warp's stop decision.
-template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE>
+template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE, bool TEAM = false>
 __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, const float4 *boxes, int n,
                                           const LinkBox &lb, const Stash &stash, FrameCursor &fc, Ctl &ctl,
-                                          bool &col, const WorkRef<STATS> &w) {
+                                          bool &col, const WorkRef<STATS> &w, const Team &team = Team{}) {
     using K = Kind<KIND>;
     constexpr int PB = 32 / LMAX > 0 ? 32 / LMAX : 1;  // primitives per batch
     constexpr unsigned kLinks = (1u << LMAX) - 1u;
     const int lane = threadIdx.x & 31;
     const int my_l = lane % LMAX, my_p = lane / LMAX;
     const bool my_on = my_p < PB && ((P.link_mask >> my_l) & 1u);
+    const int k_first = TEAM ? team.part * PB : 0, k_step = TEAM ? team.nparts * PB : PB;
 #pragma unroll 1
-    for (int k0 = 0; k0 < n; k0 += PB) {
+    for (int k0 = k_first; k0 < n; k0 += k_step) {
+        if (TEAM && *team.flag) return true;  // another warp of the team found a collision
         const int kb = k0 + my_p;
         bool ov = false;
         if (my_on && kb < n) {
@@ -569,7 +581,10 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                     const float4 sp = P.spheres[s];
                     col |= (s < L.sm ? hA : hB) && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
                 }
-                if (group_stop<MODE>(ctl, col)) return true;
+                if (group_stop<MODE>(ctl, col)) {
+                    if (TEAM && (threadIdx.x & 31) == 0) *team.flag = 1;
+                    return true;
+                }
             }
         }
     }
@@ -881,9 +896,10 @@ __device__ __forceinline__ bool pose_and_check_frequent(const RobotParams &P, co
 // the verdict.  LMAX bounds the link count (a compile-time bound for the
 // per-link loops and the cull's lane layout).
 // Returns this lane's collision flag; the warp stops early per MODE.
-template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
+template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF, bool TEAM = false>
 __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const QF &qf, const EnvSm &env,
-                                                   const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w) {
+                                                   const Stash &stash, const Ctl &ctl_in, const WorkRef<STATS> &w,
+                                                   const Team &team = Team{}) {
     bool col = false;
     Ctl ctl = ctl_in;
     const int D = P.n_joints;
@@ -925,7 +941,8 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
     for (int phase = 0; phase < 2; ++phase) {
         if ((phase == 0) != ((env.order & kOrderPrimsFirst) != 0)) {  // self pairs
             FrameCursor cur_a, cur_b;
-            for (int g = 0; g < P.n_groups; ++g) {
+            for (int g = TEAM ? team.part : 0; g < P.n_groups; g += TEAM ? team.nparts : 1) {
+                if (TEAM && *team.flag) return col;  // another warp of the team found a collision
                 const GroupC G = P.groups[g];
                 const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
                 const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
@@ -948,7 +965,10 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
                         const float r2 = sa.w + sb.w;
                         col |= h && (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2 * r2);
                     }
-                    if (group_stop<MODE>(ctl, col)) return col;
+                    if (group_stop<MODE>(ctl, col)) {
+                        if (TEAM && (threadIdx.x & 31) == 0) *team.flag = 1;
+                        return col;
+                    }
                 }
             }
         } else {  // primitives
@@ -958,14 +978,14 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
                 const int kind = (env.kind_order >> (4 * ki)) & 15;
                 bool stop;
                 if (kind == 0)
-                    stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl,
-                                                                col, w);
+                    stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc,
+                                                                      ctl, col, w, team);
                 else if (kind == 1)
-                    stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl,
-                                                                col, w);
+                    stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc,
+                                                                      ctl, col, w, team);
                 else
-                    stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl,
-                                                                col, w);
+                    stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.box, env.bb_box, env.nb, lb, stash, fc,
+                                                                      ctl, col, w, team);
                 if (stop) return col;
             }
         }

@@ -100,7 +100,11 @@ struct RRTLaunch {
     int T, cap;
     float range, res;
     float *nodes;
-    int *parent, *queue, *status, *iters;
+    int *parent;
+    int *counters;   // 3 ints of scratch: the two phases' problem counters and the set-aside count
+    int *pending;    // [B] scratch: problems the first phase set aside
+    int4 *save;      // [B] scratch: where each set-aside problem stands
+    int *status, *iters;
     float *path;
     int *path_len, *sizes;
     unsigned long long watchdog_ns;

@@ -64,6 +64,42 @@ def test_rrt_connect_matches_oracle(vpmod, name, B, T, rng, cap):
     val.close()
 
 
+@pytest.mark.parametrize("T", [300, 40])
+def test_rrt_connect_second_phase_matches_oracle(vpmod, T):
+    """Problems that outlast the first phase's 32 samples are resumed by a
+    team of warps (T = 300: most are solved there; T = 40: some run out of
+    samples there).  Endpoints are drawn where the oracle finds clearance
+    above 1 mm, so every problem plans; outcomes must match the oracle's
+    exactly wherever no edge verdict fell inside the band."""
+    Validator, vp = vpmod
+    w = vpgen.workload(vpgen.TORSO8_OBB60_CAP20, n_edges=8)
+    o = oracle.Oracle(w.robot, w.env)
+    cand = vpgen.uniform_configs(w.robot, 1200, seed=71)
+    free = cand[o.clearance(cand.astype(np.float64)) > 1e-3]
+    B = 96
+    start, goal = free[:B], free[B:2 * B]
+    samples = np.stack([vpgen.uniform_configs(w.robot, T, seed=1071 + b) for b in range(B)])
+    val = Validator(w.robot, w.env)
+    out = val.rrt_connect(torch.from_numpy(start).cuda(), torch.from_numpy(goal).cuda(),
+                          torch.from_numpy(samples).cuda(), 0.8, float(w.res), 512)
+    assert val.sync_status()[0] == vp.VP_OK
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    compared = long_runs = 0
+    for b in range(B):
+        st, it, path, band, sizes = rrt_connect(o, start[b], goal[b], samples[b], 0.8, float(w.res), 512)
+        if band:
+            continue
+        compared += 1
+        long_runs += it > 32
+        assert got["status"][b] == st and got["iters"][b] == it, b
+        assert tuple(got["tree_sizes"][b]) == sizes, b
+        if st == 1:
+            np.testing.assert_array_equal(got["path"][b, :got["path_len"][b]], path)
+        else:
+            assert got["path_len"][b] == 0
+    assert compared >= 0.8 * B and long_runs >= 5
+
+
 def test_rrt_connect_edge_cases(vpmod):
     Validator, vp = vpmod
     w = vpgen.workload(vpgen.ARM7_SPHERES16, n_edges=8)
