@@ -189,6 +189,23 @@ vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q1, float re
 vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                             float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
 
+/* Edge validity from host memory: vp_validate_edges (mode VP_MODE_PLAIN or
+ * VP_MODE_BATCHED) on host arrays, the copies overlapped with the work.
+ * q0, q1: host float [E][D]; counts: host int32 [E] or NULL; valid: host
+ * uint8 [E] (written).  The batch is cut into up to eight chunks of about
+ * 2^19 edges; each chunk's inputs go to the device on a copy stream while
+ * the previous chunk is validated on `stream`, and each chunk's verdicts
+ * come back on a second copy stream as soon as they are known.  The call
+ * returns once the work is enqueued; `stream` completes only when every
+ * verdict is in `valid`, so synchronise it before reading them and keep the
+ * host arrays alive until then.  Page-locked host memory lets the copies run
+ * asynchronously; pageable memory works but serialises them.  The context
+ * keeps device copies of the arrays (grown on demand, which synchronises the
+ * device).  Verdicts equal vp_validate_edges' on the same arrays; the
+ * kernel-time hook does not time this call. */
+vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                 float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream);
+
 /* Work counters for the FLOP model: edge validation in `mode` (VP_MODE_PLAIN
  * or VP_MODE_BATCHED, the latter launched directly rather than from its
  * graph) with counters of the work done (VP_WORK_* indices) added into `work`

@@ -64,6 +64,16 @@ class Validator:
         vp.vp_validate_edges(self.ctx, q0, q1, counts, float(resolution), out, mode, stream)
         return out
 
+    def validate_edges_host(self, q0, q1, counts=None, resolution=1.0 / 32.0, mode=vp.VP_MODE_PLAIN, stream=None,
+                            out=None):
+        """Edge validation from host (CPU, ideally pinned) tensors, the copies
+        overlapped with the work; returns the CPU uint8 verdicts, valid once
+        `stream` has completed (synchronise it before reading)."""
+        if out is None:
+            out = torch.empty(q0.shape[0], dtype=torch.uint8, pin_memory=True)
+        vp.vp_validate_edges_host(self.ctx, q0, q1, counts, float(resolution), out, mode, stream)
+        return out
+
     def validate_edges_work(self, q0, q1, counts=None, resolution=1.0 / 32.0, mode=vp.VP_MODE_PLAIN, stream=None):
         out = torch.empty(q0.shape[0], dtype=torch.uint8, device=self._dev())
         work = torch.zeros(vp.VP_WORK_N, dtype=torch.int64, device=self._dev())

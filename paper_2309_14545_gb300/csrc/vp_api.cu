@@ -43,6 +43,14 @@ struct vp_ctx {
     float *rrt_nodes = nullptr;
     int *rrt_parent = nullptr, *rrt_queue = nullptr;  // rrt_queue: 3 counters
     int *rrt_pending = nullptr;                        // [B] ints, then [B] int4 (saved states)
+    // vp_validate_edges_host: device copies of the caller's host arrays, the
+    // copy streams and the events that chain the chunks
+    float *hx_q0 = nullptr, *hx_q1 = nullptr;
+    int32_t *hx_counts = nullptr;
+    uint8_t *hx_valid = nullptr;
+    size_t hx_cap_q = 0, hx_cap_e = 0;
+    cudaStream_t hx_in = nullptr, hx_out = nullptr;
+    cudaEvent_t hx_ev[2 * 8 + 2] = {};
     size_t rrt_node_cap = 0, rrt_parent_cap = 0, rrt_pending_cap = 0;
     FkCodegen fk_gen;            // per-robot FK compiled at run time (vp_fk_codegen)
     int fk_mode = -1;            // 1 generated, 0 table-driven, -1 automatic (generated once it builds)
@@ -144,6 +152,14 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->rrt_parent) cudaFree(ctx->rrt_parent);
         if (ctx->rrt_queue) cudaFree(ctx->rrt_queue);
         if (ctx->rrt_pending) cudaFree(ctx->rrt_pending);
+        cudaFree(ctx->hx_q0);
+        cudaFree(ctx->hx_q1);
+        cudaFree(ctx->hx_counts);
+        cudaFree(ctx->hx_valid);
+        if (ctx->hx_in) cudaStreamDestroy(ctx->hx_in);
+        if (ctx->hx_out) cudaStreamDestroy(ctx->hx_out);
+        for (cudaEvent_t ev : ctx->hx_ev)
+            if (ev) cudaEventDestroy(ev);
         fk_codegen_release(&ctx->fk_gen);
     }
     delete ctx;
@@ -700,6 +716,87 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
 extern "C" vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                                        float resolution, int64_t n_edges, uint8_t *valid, int mode, void *stream) {
     return validate_edges_impl(ctx, q0, q1, counts, resolution, n_edges, valid, mode, nullptr, stream);
+}
+
+extern "C" vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
+                                            float resolution, int64_t n_edges, uint8_t *valid, int mode,
+                                            void *stream) {
+    vp_status s = check_loaded(ctx);
+    if (s != VP_OK) return s;
+    if (n_edges < 0) return fail(ctx, VP_ERR_ARG, "n_edges < 0");
+    if (!counts && (!(resolution > 0.f) || !std::isfinite(resolution)))
+        return fail(ctx, VP_ERR_ARG, "resolution must be > 0 when counts is NULL");
+    if (mode != VP_MODE_PLAIN && mode != VP_MODE_BATCHED)
+        return fail(ctx, VP_ERR_ARG, "vp_validate_edges_host: mode must be VP_MODE_PLAIN or VP_MODE_BATCHED");
+    if (n_edges == 0) return VP_OK;
+    if (!q0 || !q1 || !valid) return fail(ctx, VP_ERR_ARG, "NULL buffer");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int D = ctx->robot.n_joints;
+    const size_t nq = static_cast<size_t>(n_edges) * D, ne = static_cast<size_t>(n_edges);
+    cudaError_t e = cudaSuccess;
+    if (nq > ctx->hx_cap_q || ne > ctx->hx_cap_e) {  // grow the device copies (waits for queued work)
+        e = cudaDeviceSynchronize();
+        cudaFree(ctx->hx_q0);
+        cudaFree(ctx->hx_q1);
+        cudaFree(ctx->hx_counts);
+        cudaFree(ctx->hx_valid);
+        ctx->hx_q0 = ctx->hx_q1 = nullptr;
+        ctx->hx_counts = nullptr;
+        ctx->hx_valid = nullptr;
+        ctx->hx_cap_q = ctx->hx_cap_e = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hx_q0, nq * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hx_q1, nq * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hx_counts, ne * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->hx_valid, ne);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges_host (device copies)");
+        ctx->hx_cap_q = nq;
+        ctx->hx_cap_e = ne;
+    }
+    if (!ctx->hx_in) e = cudaStreamCreateWithFlags(&ctx->hx_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->hx_out) e = cudaStreamCreateWithFlags(&ctx->hx_out, cudaStreamNonBlocking);
+    for (cudaEvent_t &ev : ctx->hx_ev)
+        if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges_host (streams)");
+    // chunks of about 2^19 edges (at most 8): the copies of chunk i+1 overlap
+    // the validation of chunk i, and each chunk's verdicts go back as soon
+    // as they are known
+    const int64_t n_chunks = std::max<int64_t>(1, std::min<int64_t>(8, (n_edges + (1 << 19) - 1) >> 19));
+    const int64_t per = (n_edges + n_chunks - 1) / n_chunks;
+    cudaEvent_t *ev_in = ctx->hx_ev, *ev_out = ctx->hx_ev + 8, ev_start = ctx->hx_ev[16], ev_done = ctx->hx_ev[17];
+    // the copies wait for earlier work on the caller's stream (which may
+    // still read the device copies)
+    e = cudaEventRecord(ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hx_in, ev_start, 0);
+    const bool timing = ctx->timing;
+    ctx->timing = false;  // the kernel-time hook times single-launch calls
+    vp_status rs = VP_OK;
+    for (int64_t c = 0; c < n_chunks && e == cudaSuccess && rs == VP_OK; ++c) {
+        const int64_t off = c * per, n = std::min<int64_t>(per, n_edges - off);
+        if (n <= 0) break;
+        const size_t qo = static_cast<size_t>(off) * D, qn = static_cast<size_t>(n) * D * sizeof(float);
+        e = cudaMemcpyAsync(ctx->hx_q0 + qo, q0 + qo, qn, cudaMemcpyHostToDevice, ctx->hx_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hx_q1 + qo, q1 + qo, qn, cudaMemcpyHostToDevice, ctx->hx_in);
+        if (e == cudaSuccess && counts)
+            e = cudaMemcpyAsync(ctx->hx_counts + off, counts + off, n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                ctx->hx_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], ctx->hx_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in[c], 0);
+        if (e != cudaSuccess) break;
+        rs = validate_edges_impl(ctx, ctx->hx_q0 + qo, ctx->hx_q1 + qo, counts ? ctx->hx_counts + off : nullptr,
+                                 resolution, n, ctx->hx_valid + off, mode, nullptr, stream);
+        if (rs != VP_OK) break;
+        e = cudaEventRecord(ev_out[c], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hx_out, ev_out[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(valid + off, ctx->hx_valid + off, n, cudaMemcpyDeviceToHost, ctx->hx_out);
+    }
+    ctx->timing = timing;
+    if (rs != VP_OK) return rs;
+    // the caller's stream completes only once every verdict is on the host
+    if (e == cudaSuccess) e = cudaEventRecord(ev_done, ctx->hx_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_done, 0);
+    return e == cudaSuccess ? VP_OK : cuda_fail(ctx, e, "vp_validate_edges_host");
 }
 
 extern "C" vp_status vp_validate_edges_work(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,

@@ -38,7 +38,7 @@ EXPORTS = ("vp_create", "vp_destroy", "vp_last_error", "vp_load_robot", "vp_load
            "vp_collision_cost", "vp_autotune", "vp_sync_status", "vp_validate_edges_noalloc",
            "vp_kernel_time", "vp_set_watchdog", "vp_tiling", "vp_set_tiling", "vp_set_screen_rounds",
            "vp_screen_rounds", "vp_set_check_order", "vp_check_order", "vp_measure_fp32_peak", "vp_nearest",
-           "vp_shortcut_paths", "vp_rrt_connect", "vp_fk_codegen", "vp_link_bounds")
+           "vp_shortcut_paths", "vp_rrt_connect", "vp_fk_codegen", "vp_link_bounds", "vp_validate_edges_host")
 
 
 class VPError(RuntimeError):
@@ -93,6 +93,7 @@ def _load_lib():
         "vp_rrt_connect": (U, [P, P, P, I64, P, C.c_int32, F, F, C.c_int32, P, P, P, P, P, P]),
         "vp_fk_codegen": (U, [P, C.c_int, C.POINTER(C.c_double)]),
         "vp_link_bounds": (U, [P, C.c_int, P, P, P]),
+        "vp_validate_edges_host": (U, [P, P, P, P, F, I64, P, C.c_int, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +125,21 @@ def _dev(t, dtype, name, shape=None):
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.data_ptr() if t.numel() else None
+
+
+def _host(t, dtype, name, shape=None):
+    """Host pointer of a contiguous CPU tensor of the given dtype (None -> NULL)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a CPU tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -211,6 +227,16 @@ def vp_validate_edges(ctx, q0, q1, counts, resolution, valid, mode=VP_MODE_PLAIN
                                       _dev(q1, torch.float32, "q1", q0.shape),
                                       _dev(counts, torch.int32, "counts", (E,)), C.c_float(resolution), E,
                                       _dev(valid, torch.uint8, "valid", (E,)), int(mode), _stream(stream)))
+
+
+def vp_validate_edges_host(ctx, q0, q1, counts, resolution, valid, mode=VP_MODE_PLAIN, stream=None):
+    """q0, q1, counts, valid: CPU tensors (page-locked for overlapped copies);
+    the verdicts are in valid once `stream` has completed."""
+    E = q0.shape[0]
+    _check(ctx, lib.vp_validate_edges_host(ctx, _host(q0, torch.float32, "q0"),
+                                           _host(q1, torch.float32, "q1", q0.shape),
+                                           _host(counts, torch.int32, "counts", (E,)), C.c_float(resolution), E,
+                                           _host(valid, torch.uint8, "valid", (E,)), int(mode), _stream(stream)))
 
 
 def vp_validate_edges_work(ctx, q0, q1, counts, resolution, valid, mode, work, stream=None):
