@@ -192,10 +192,12 @@ vp_status vp_validate_edges(vp_ctx *ctx, const float *q0, const float *q1, const
 /* Edge validity from host memory: vp_validate_edges (mode VP_MODE_PLAIN or
  * VP_MODE_BATCHED) on host arrays, the copies overlapped with the work.
  * q0, q1: host float [E][D]; counts: host int32 [E] or NULL; valid: host
- * uint8 [E] (written).  The batch is cut into up to eight chunks of about
- * 2^19 edges; each chunk's inputs go to the device on a copy stream while
- * the previous chunk is validated on `stream`, and each chunk's verdicts
- * come back on a second copy stream as soon as they are known.  The call
+ * uint8 [E] (written).  The batch is cut into chunks -- in VP_MODE_PLAIN up
+ * to eight of about 2^19 edges, in VP_MODE_BATCHED (where each launch has a
+ * fixed cost) a quarter and the rest once E >= 2^20 -- and each chunk's
+ * inputs go to the device on a copy stream while the previous chunk is
+ * validated on `stream`; each chunk's verdicts come back on a second copy
+ * stream as soon as they are known.  The call
  * returns once the work is enqueued; `stream` completes only when every
  * verdict is in `valid`, so synchronise it before reading them and keep the
  * host arrays alive until then.  Page-locked host memory lets the copies run

@@ -758,11 +758,25 @@ extern "C" vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const 
     for (cudaEvent_t &ev : ctx->hx_ev)
         if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges_host (streams)");
-    // chunks of about 2^19 edges (at most 8): the copies of chunk i+1 overlap
-    // the validation of chunk i, and each chunk's verdicts go back as soon
-    // as they are known
-    const int64_t n_chunks = std::max<int64_t>(1, std::min<int64_t>(8, (n_edges + (1 << 19) - 1) >> 19));
-    const int64_t per = (n_edges + n_chunks - 1) / n_chunks;
+    // chunks: the copies of chunk i+1 overlap the validation of chunk i, and
+    // each chunk's verdicts go back as soon as they are known.  The plain
+    // kernel takes chunks of about 2^19 edges (at most 8).  Each batched
+    // launch costs about half a millisecond beyond its edges (the bucketing,
+    // and the persistent kernels' start and tail), so a large batch goes in
+    // two: a quarter, validated while the other three quarters are copied,
+    // then the rest.
+    int64_t bounds[9] = {0};
+    int n_chunks = 1;
+    if (mode == VP_MODE_BATCHED) {
+        if (n_edges >= (int64_t{1} << 20)) {
+            bounds[1] = n_edges / 4;
+            n_chunks = 2;
+        }
+    } else {
+        n_chunks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (n_edges + (1 << 19) - 1) >> 19)));
+        for (int c = 1; c < n_chunks; ++c) bounds[c] = n_edges * c / n_chunks;
+    }
+    bounds[n_chunks] = n_edges;
     cudaEvent_t *ev_in = ctx->hx_ev, *ev_out = ctx->hx_ev + 8, ev_start = ctx->hx_ev[16], ev_done = ctx->hx_ev[17];
     // the copies wait for earlier work on the caller's stream (which may
     // still read the device copies)
@@ -771,9 +785,9 @@ extern "C" vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const 
     const bool timing = ctx->timing;
     ctx->timing = false;  // the kernel-time hook times single-launch calls
     vp_status rs = VP_OK;
-    for (int64_t c = 0; c < n_chunks && e == cudaSuccess && rs == VP_OK; ++c) {
-        const int64_t off = c * per, n = std::min<int64_t>(per, n_edges - off);
-        if (n <= 0) break;
+    for (int c = 0; c < n_chunks && e == cudaSuccess && rs == VP_OK; ++c) {
+        const int64_t off = bounds[c], n = bounds[c + 1] - bounds[c];
+        if (n <= 0) continue;
         const size_t qo = static_cast<size_t>(off) * D, qn = static_cast<size_t>(n) * D * sizeof(float);
         e = cudaMemcpyAsync(ctx->hx_q0 + qo, q0 + qo, qn, cudaMemcpyHostToDevice, ctx->hx_in);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->hx_q1 + qo, q1 + qo, qn, cudaMemcpyHostToDevice, ctx->hx_in);

@@ -21,7 +21,8 @@ def vpmod(cuda_ok):
     return Validator, vp
 
 
-@pytest.mark.parametrize("name,n", [(vpgen.DUAL14_MIXED1000, 1_200_003), (vpgen.TORSO8_OBB60_CAP20, 777),
+@pytest.mark.parametrize("name,n", [(vpgen.DUAL14_MIXED1000, 1_200_003), (vpgen.TORSO8_OBB60_CAP20, 1_100_001),
+                                    (vpgen.TORSO8_OBB60_CAP20, 777),
                                     (vpgen.ARM7_SPHERES16, 1)])
 def test_host_equals_device(vpmod, name, n):
     Validator, vp = vpmod
