@@ -12,10 +12,6 @@
 //    global counter.  A work item of bucket b packs 32/G_b edges into lane
 //    groups of G_b lanes; the groups run the raked check in lockstep and the
 //    warp leaves a state as soon as every group has a collision or is done.
-//    Edges still undecided after the screening rounds are published to a
-//    second-phase list that warps out of screening items take from in the
-//    same launch (each edge in kSplit items over whole warps), so the two
-//    phases share one launch and one tail.
 // The three launches (plus the counter reset) are captured once into a CUDA
 // graph per buffer set and replayed.  G_b comes from the autotuner, which
 // times each bucket alone, at full occupancy, with every group size and keeps
@@ -107,6 +103,9 @@ BatchedKernel batched_kernel_for(const RobotParams &P, bool stats, bool staged, 
     return kernel_set(lmax_for(P.n_links)).batched[family_of(order)][stats][P.simple != 0][staged];
 }
 
+SurvivorsKernel survivors_kernel_for(const RobotParams &P, bool stats, bool staged, int order) {
+    return kernel_set(lmax_for(P.n_links)).survivors[family_of(order)][stats][P.simple != 0][staged];
+}
 
 size_t batched_smem(const EnvView &env, const RobotParams &P) {
     return env_smem_bytes(env) + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
@@ -223,10 +222,12 @@ int prepare_kernel(const BatchedArgs &a, EnvView *view, size_t *smem, int *grid,
         const int order = fam == kFamFrequent ? kOrderFrequent : (fam == kFamInterleave ? kOrderInterleave : 0);
         for (int stats = 0; stats < 2; ++stats)
             for (int staged = 0; staged < 2; ++staged) {
-                const void *f = reinterpret_cast<const void *>(batched_kernel_for(*a.robot, stats, staged, order));
+                const void *k[2] = {reinterpret_cast<const void *>(batched_kernel_for(*a.robot, stats, staged, order)),
+                                    reinterpret_cast<const void *>(survivors_kernel_for(*a.robot, stats, staged, order))};
                 const size_t m = staged ? m_max : m_in;
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m));
+                for (const void *f : k)
+                    if (e == cudaSuccess)
+                        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m));
             }
         int bi = 0, bs = 0;
         if (e == cudaSuccess)
@@ -256,9 +257,6 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const B
                     cudaStream_t s, uint8_t *valid, unsigned long long *work = nullptr) {
     const int D = a.robot->n_joints;
     cudaError_t e = cudaMemsetAsync(im->ctrl, 0, kCtrlInts * sizeof(int), s);
-    // second-phase entries start as (-1, -1): a reader waits until its
-    // entry's producer has written it
-    if (e == cudaSuccess) e = cudaMemsetAsync(im->surv, 0xff, static_cast<size_t>(a.E) * sizeof(int2), s);
     if (e != cudaSuccess) return e;
     const unsigned nb = static_cast<unsigned>((a.E + 255) / 256);
     bucket_count_kernel<<<nb, 256, 0, s>>>(D, a.q0, a.q1, a.counts, a.res, a.E, im->kbuf, valid, a.status, im->ctrl);
@@ -269,6 +267,10 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const B
     batched_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
                                                                             plan, valid, a.status, im->ctrl, im->surv,
                                                                             work);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    survivors_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+                                                                              plan, valid, a.status, im->ctrl, work);
     e = cudaGetLastError();
     if (e == cudaSuccess && a.ev_stop) e = cudaEventRecordWithFlags(a.ev_stop, s, cudaEventRecordExternal);
     return e;
@@ -448,15 +450,14 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     auto time_plan = [&](float *ms_out) {
         float best = 1e30f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-            // both queues, the survivor count and the finished-item count;
-            // the survivor entries back to (-1, -1)
-            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, 4 * sizeof(int), s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(im->surv, 0xff, static_cast<size_t>(S) * sizeof(int2), s);
+            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, 3 * sizeof(int), s);  // both queues, survivor count
             if (e != cudaSuccess) break;
             cudaEventRecord(t0, s);
             batched_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
                                                                            p, tv, a.status, im->ctrl, im->surv,
                                                                            nullptr);
+            survivors_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
+                                                                             p, tv, a.status, im->ctrl, nullptr);
             cudaEventRecord(t1, s);
             e = cudaEventSynchronize(t1);
             if (e == cudaSuccess) e = cudaGetLastError();

@@ -17,8 +17,7 @@ constexpr int kCtrlHist = 0;     // ctrl[0..8]   edges per bucket
 constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
 constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
 constexpr int kCtrlSurv = 33;    // ctrl[33]     edges left to the second phase
-constexpr int kCtrlQueue2 = 34;  // ctrl[34]     second-phase work-item tickets
-constexpr int kCtrlDone = 35;    // ctrl[35]     screening items finished (their survivors published)
+constexpr int kCtrlQueue2 = 34;  // ctrl[34]     second-phase work-item counter
 constexpr int kCtrlInts = 64;
 constexpr int kSplit = 16;       // second-phase work items per edge
 constexpr int kDefaultScreenRounds = 0;
@@ -37,9 +36,12 @@ using PlainKernel = void (*)(RobotParams, EnvView, const float *, const float *,
                              uint8_t *, unsigned *, unsigned long long *);
 using BatchedKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
                                uint8_t *, unsigned *, int *, int2 *, unsigned long long *);
+using SurvivorsKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
+                                 uint8_t *, unsigned *, int *, unsigned long long *);
 struct KernelSet {
     PlainKernel plain[3][2][2][2];  // [family][stats][simple][staged]
     BatchedKernel batched[3][2][2][2];
+    SurvivorsKernel survivors[3][2][2][2];
 };
 // The instances of one link bound and family, each from its own compilation
 // of vp_inst.cu.

@@ -164,47 +164,6 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 5) edges_plain_kernel(const __grid_co
     }
 }
 
-// One second-phase item: edge e (k states) was left undecided by the
-// screening rounds (mostly a collision-free edge, which needs every state
-// checked).  Each such edge is split into kSplit items of consecutive rounds
-// of a 32-lane raked pass over it (lane l, round r: state l R + r,
-// R = ceil(k / 32)), so one long edge is spread over many warps instead of
-// holding one lane group for all its rounds.  A collision clears the edge's
-// verdict; an item of an edge already found colliding stops.
-template <int FAM, bool STATS, int LMAX, bool SIMPLE>
-__device__ __forceinline__ void second_phase_item(const RobotParams &P, const EnvSm &es, const Stash &stash,
-                                                  const float *__restrict__ q0, const float *__restrict__ q1, int e,
-                                                  int k, int c, float *wq0, float *wdq, uint8_t *valid, Work &wk) {
-    const int lane = threadIdx.x & 31;
-    const int D = P.n_joints;
-    const int R = (k + 31) / 32, RC = (R + kSplit - 1) / kSplit;
-    const int r0 = c * RC, r1 = min(R, r0 + RC);
-    if (r0 >= r1) return;
-    volatile uint8_t *vvalid = valid;
-    __syncwarp();
-    for (int d = lane; d < D; d += 32) {
-        const float a = q0[static_cast<long long>(e) * D + d];
-        wq0[d] = a;
-        wdq[d] = q1[static_cast<long long>(e) * D + d] - a;
-    }
-    __syncwarp();
-    const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
-    for (int r = r0; r < r1; ++r) {
-        if (__shfl_sync(kFull, lane == 0 ? static_cast<int>(vvalid[e]) : 0, 0) == 0) break;  // decided elsewhere
-        int i = lane * R + r;
-        const WorkRef<STATS> w{&wk, i < k};
-        if (i >= k) i = k - 1;
-        const float t = static_cast<float>(i) * inv;
-        const bool col = check_state<FAM, kStopAny, STATS, LMAX, SIMPLE>(
-            P, [t, wq0, wdq](int jj) { return fmaf(t, wdq[jj], wq0[jj]); }, es, stash, Ctl{kFull, false}, w);
-        if (__any_sync(kFull, col)) {
-            if (lane == 0) vvalid[e] = 0;
-            break;
-        }
-    }
-    __syncwarp();
-}
-
 // Persistent validation of bucketed edges; see the file comment.  STATS adds
 // the work counters (VP_WORK_*) of the lanes that hold a state of a live edge.
 template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
@@ -264,77 +223,18 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
     }
 
-    volatile int *vctrl = ctrl;
-    volatile unsigned long long *vsurv = reinterpret_cast<volatile unsigned long long *>(surv);
-    bool screening = true;  // this warp still takes screening items
     while (true) {
-        // the next work item: a screening item while any is left, then a
-        // second-phase ticket, which waits (bounded by the watchdog) until
-        // the survivors published so far cover it, or the screening is over
-        // and they never will
-        int item = 0, kind = 0;  // kind 1: screening item, 2: second-phase item, 0: no more work
+        int item = 0;
         if (lane == 0) {
             if (global_ns() - t_start >= plan.watchdog_ns) {
                 atomicOr(status, VP_DEVERR_TIMEOUT);
+                item = -1;
             } else {
-                if (screening) {
-                    item = atomicAdd(&ctrl[kCtrlQueue], 1);
-                    if (item < s_items)
-                        kind = 1;
-                    else
-                        screening = false;
-                }
-                if (!screening) {
-                    item = atomicAdd(&ctrl[kCtrlQueue2], 1);
-                    while (true) {
-                        if (item < static_cast<long long>(vctrl[kCtrlSurv]) * kSplit) {
-                            kind = 2;
-                            break;
-                        }
-                        if (vctrl[kCtrlDone] >= s_items) {  // every survivor is published
-                            __threadfence();
-                            kind = item < static_cast<long long>(vctrl[kCtrlSurv]) * kSplit ? 2 : 0;
-                            break;
-                        }
-                        if (global_ns() - t_start >= plan.watchdog_ns) {
-                            atomicOr(status, VP_DEVERR_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(256);
-                    }
-                }
+                item = atomicAdd(&ctrl[kCtrlQueue], 1);
             }
         }
-        kind = __shfl_sync(kFull, kind, 0);
         item = __shfl_sync(kFull, item, 0);
-        if (kind == 0) break;
-        if (kind == 2) {
-            // second phase: the item's edge, once its producer has written it
-            int2 ek = make_int2(-1, 0);
-            if (lane == 0) {
-                const int si = item / kSplit;
-                while (true) {
-                    const unsigned long long v = vsurv[si];
-                    if (static_cast<int>(v & 0xffffffffu) >= 0) {
-                        ek = make_int2(static_cast<int>(v & 0xffffffffu), static_cast<int>(v >> 32));
-                        break;
-                    }
-                    if (global_ns() - t_start >= plan.watchdog_ns) {
-                        atomicOr(status, VP_DEVERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                __threadfence();  // the producer's verdict store is visible from here on
-            }
-            ek.x = __shfl_sync(kFull, ek.x, 0);
-            ek.y = __shfl_sync(kFull, ek.y, 0);
-            if (ek.x >= 0)
-                second_phase_item<FAM, STATS, LMAX, SIMPLE>(P, es, stash, q0, q1, ek.x, ek.y, item % kSplit, wbuf,
-                                                           wbuf + 16, valid, wk);
-            flush_work<STATS>(wk, work, lane);
-            continue;
-        }
+        if (item < 0 || item >= s_items) break;
         int b = kNB - 1;
         while (b > 0 && item >= s_item_end[b]) --b;
         const int first_item = (b == kNB - 1) ? 0 : s_item_end[b + 1];
@@ -395,21 +295,108 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
             if (__all_sync(kFull, done)) break;
         }
         // an edge the screening rounds left undecided goes to the second phase
-        // (valid until one of its work items there finds a collision): its
-        // verdict first, then its entry, each made visible before the next
+        // (valid until one of its work items there finds a collision)
         if (!done && j == 0) {
+            surv[atomicAdd(&ctrl[kCtrlSurv], 1)] = make_int2(e, k);
             valid[e] = 1;
-            __threadfence();
-            const int si = atomicAdd(&ctrl[kCtrlSurv], 1);
-            vsurv[si] = (static_cast<unsigned long long>(static_cast<unsigned>(k)) << 32) | static_cast<unsigned>(e);
             if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
         }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            atomicAdd(&ctrl[kCtrlDone], 1);  // this item's survivors are all published
+        if constexpr (STATS) {
+#pragma unroll
+            for (int c = 0; c < VP_WORK_N; ++c) {
+                const unsigned sum = __reduce_add_sync(kFull, wk.v[c]);
+                if (lane == 0 && sum) atomicAdd(work + c, static_cast<unsigned long long>(sum));
+                wk.v[c] = 0;
+            }
         }
-        flush_work<STATS>(wk, work, lane);
+    }
+}
+
+// Second phase: the edges the screening rounds left undecided (mostly
+// collision-free ones, which need every state checked).  Each is split into
+// kSplit work items of consecutive rounds of a 32-lane raked pass over the
+// edge (lane l, round r: state l R + r, R = ceil(k / 32)), so one long edge
+// is spread over many warps instead of holding one lane group for all its
+// rounds.  A collision clears the edge's verdict; items of an edge already
+// found colliding are skipped.
+template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
+__global__ void VP_VALIDATION_BOUNDS(LMAX, 6) survivors_kernel(
+    const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
+    const float *__restrict__ q1, const int2 *__restrict__ surv, const BatchPlan plan, uint8_t *valid,
+    unsigned *status, int *ctrl, unsigned long long *work) {
+    const int n_items = ctrl[kCtrlSurv] * kSplit;  // written by the screening launch
+    if (n_items == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    size_t off = STAGED ? static_cast<size_t>(env.n_float4) * 16 : 0;
+    float4 *env_sm = reinterpret_cast<float4 *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
+    off += 16;
+    float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
+    off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
+    Stash stash;
+    stash.frames = nullptr;
+    stash.centres = reinterpret_cast<float *>(smem + off);
+    off += static_cast<size_t>(P.n_links) * kCentreFloats * kBlock * sizeof(float);
+    stash.motion = reinterpret_cast<float *>(smem + off);
+    stash.stride = kBlock;
+    if (STAGED && !stage_env(env_sm, env, bar, status)) return;
+    const EnvSm es = env_views<STAGED>(env_sm, env);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int D = P.n_joints;
+    float *wq0 = gbuf + wib * 8 * 32, *wdq = wq0 + 16;
+    volatile uint8_t *vvalid = valid;
+    const uint64_t t_start = global_ns();
+    Work wk;
+    if (STATS) {
+#pragma unroll
+        for (int i = 0; i < VP_WORK_N; ++i) wk.v[i] = 0;
+    }
+    while (true) {
+        int item = 0;
+        if (lane == 0) {
+            if (global_ns() - t_start >= plan.watchdog_ns) {
+                atomicOr(status, VP_DEVERR_TIMEOUT);
+                item = -1;
+            } else {
+                item = atomicAdd(&ctrl[kCtrlQueue2], 1);
+            }
+        }
+        item = __shfl_sync(kFull, item, 0);
+        if (item < 0 || item >= n_items) break;
+        const int2 ek = surv[item / kSplit];
+        const int e = ek.x, k = ek.y, c = item % kSplit;
+        const int R = (k + 31) / 32, RC = (R + kSplit - 1) / kSplit;
+        const int r0 = c * RC, r1 = min(R, r0 + RC);
+        if (r0 >= r1) continue;
+        __syncwarp();
+        for (int d = lane; d < D; d += 32) {
+            const float a = q0[static_cast<long long>(e) * D + d];
+            wq0[d] = a;
+            wdq[d] = q1[static_cast<long long>(e) * D + d] - a;
+        }
+        __syncwarp();
+        const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
+        for (int r = r0; r < r1; ++r) {
+            if (__shfl_sync(kFull, lane == 0 ? static_cast<int>(vvalid[e]) : 0, 0) == 0) break;  // decided elsewhere
+            int i = lane * R + r;
+            const WorkRef<STATS> w{&wk, i < k};
+            if (i >= k) i = k - 1;
+            const float t = static_cast<float>(i) * inv;
+            const bool col = check_state<FAM, kStopAny, STATS, LMAX, SIMPLE>(
+                P, [t, wq0, wdq](int jj) { return fmaf(t, wdq[jj], wq0[jj]); }, es, stash, Ctl{kFull, false}, w);
+            if (__any_sync(kFull, col)) {
+                if (lane == 0) vvalid[e] = 0;
+                break;
+            }
+        }
+        if constexpr (STATS) {
+#pragma unroll
+            for (int q = 0; q < VP_WORK_N; ++q) {
+                const unsigned sum = __reduce_add_sync(kFull, wk.v[q]);
+                if (lane == 0 && sum) atomicAdd(work + q, static_cast<unsigned long long>(sum));
+                wk.v[q] = 0;
+            }
+        }
     }
 }
 
@@ -430,6 +417,12 @@ void fill_kernel_set(KernelSet &s) {
     s.batched[FAM][0][1][1] = edges_batched_kernel<false, LMAX, true, true, FAM>;
     s.batched[FAM][1][0][0] = s.batched[FAM][1][1][0] = edges_batched_kernel<true, LMAX, false, false, FAM>;
     s.batched[FAM][1][0][1] = s.batched[FAM][1][1][1] = edges_batched_kernel<true, LMAX, false, true, FAM>;
+    s.survivors[FAM][0][0][0] = survivors_kernel<false, LMAX, false, false, FAM>;
+    s.survivors[FAM][0][0][1] = survivors_kernel<false, LMAX, false, true, FAM>;
+    s.survivors[FAM][0][1][0] = survivors_kernel<false, LMAX, true, false, FAM>;
+    s.survivors[FAM][0][1][1] = survivors_kernel<false, LMAX, true, true, FAM>;
+    s.survivors[FAM][1][0][0] = s.survivors[FAM][1][1][0] = survivors_kernel<true, LMAX, false, false, FAM>;
+    s.survivors[FAM][1][0][1] = s.survivors[FAM][1][1][1] = survivors_kernel<true, LMAX, false, true, FAM>;
 }
 
 }  // namespace vp
