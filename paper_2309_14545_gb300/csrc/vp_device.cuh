@@ -63,13 +63,38 @@ __device__ __forceinline__ void joint_motion(const JointC &J, float q, float &s,
     }
 }
 
+// (sin q, cos q) for the collision checks: the SFU approximations
+// (__sincosf) after reducing q to [-pi, pi] by Cody and Waite's method (2 pi
+// split into a head of 8 significant bits, whose products with the small
+// integer k are exact, and the tail 2 pi - head).  On [-pi, pi] the
+// approximations' absolute error is at most 2^-21.41 (3.6e-7), so a chain of
+// n revolute joints displaces a point at distance d from them by at most
+// about n * 3.6e-7 * d: under 4e-6 m for seven joints within 1.5 m, far
+// inside the boundary band of the verdicts.  FK, the cost and its gradient
+// keep the accurate sincosf.
+__device__ __forceinline__ void sincos_reduced(float q, float &s, float &c) {
+    constexpr float kInv2Pi = 0.159154943f, kHead = 6.28125f, kTail = 1.93530717958e-3f;
+    const float k = rintf(q * kInv2Pi);
+    __sincosf(fmaf(-k, kTail, fmaf(-k, kHead, q)), &s, &c);
+}
+
+// joint_motion for the collision checks (sincos_reduced)
+__device__ __forceinline__ void joint_motion_check(const JointC &J, float q, float &s, float &c) {
+    if (J.meta & kMetaPrismatic) {
+        s = q;
+        c = 0.f;
+    } else {
+        sincos_reduced(q, s, c);
+    }
+}
+
 // The same, out of line: the frequent-first order poses joints from more
-// than one place, and a single copy of the sine and cosine code there keeps
-// the kernel's instructions in cache (9% faster on 1,000 primitives; the
-// pose-all and interleaved loops keep the inlined copy, which they pose
-// from once).
+// than one place, and a single copy of the code there keeps the kernel's
+// instructions in cache (9% faster on 1,000 primitives with the accurate
+// sincosf; the pose-all and interleaved loops keep the inlined copy, which
+// they pose from once).
 static __device__ __noinline__ void joint_motion_outlined(const JointC &J, float q, float &s, float &c) {
-    joint_motion(J, q, s, c);
+    joint_motion_check(J, q, s, c);
 }
 
 // f <- f * origin_j * M_j: one joint of the chain, from its motion
@@ -483,8 +508,20 @@ __device__ __forceinline__ float warp_max(float v) {
     return r;
 }
 
+// A primitive's world box [lo, hi] against a warp-wide box.
+__device__ __forceinline__ bool box_hits(const float4 &lo, const float4 &hi, const LinkBox &b) {
+    return (lo.x <= b.hx) & (hi.x >= b.lx) & (lo.y <= b.hy) & (hi.y >= b.ly) & (lo.z <= b.hz) & (hi.z >= b.lz);
+}
+
+// The two levels of the primitive cull: this lane's link box (link t mod
+// LMAX), and the box of every live link at once (their union, the same in
+// every lane).
+struct WarpBoxes {
+    LinkBox link, all;
+};
+
 template <int LMAX>
-__device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const Stash &stash, bool live) {
+__device__ __forceinline__ WarpBoxes warp_link_boxes(const RobotParams &P, const Stash &stash, bool live) {
     const float inf = __int_as_float(0x7f800000);
     const int my_l = (threadIdx.x & 31) % LMAX;
     LinkBox b{inf, inf, inf, -inf, -inf, -inf};
@@ -499,7 +536,10 @@ __device__ __forceinline__ LinkBox warp_link_boxes(const RobotParams &P, const S
                     hz = warp_max(live ? c.z + r : -inf);
         if (my_l == l) b = LinkBox{lx, ly, lz, hx, hy, hz};
     }
-    return b;
+    // lanes of links outside the mask hold the empty box, which leaves the
+    // union unchanged
+    const LinkBox u{warp_min(b.lx), warp_min(b.ly), warp_min(b.lz), warp_max(b.hx), warp_max(b.hy), warp_max(b.hz)};
+    return WarpBoxes{b, u};
 }
 
 // A team of warps checking the same states together (the RRT-Connect
@@ -514,15 +554,18 @@ struct Team {
 
 // Every primitive of one kind (largest first) against every link's bounding
 // sphere, then the fine spheres of each link some lane's coarse test hit.
-// Primitives go in batches of 32 / LMAX: lane t compares the world box of
-// primitive t / LMAX of the batch with link t mod LMAX's warp-wide box, and
-// a ballot leaves the (link, primitive) pairs whose boxes overlap; only those
-// take the exact ball test.  The cull is conservative (the primitive boxes
-// carry a rounding margin), so the verdicts are those of testing every pair.
-// Returns the warp's stop decision.
+// The cull has two levels.  Primitives go in batches of 32, lane t comparing
+// the world box of primitive t of the batch with the union of the live
+// links' warp-wide boxes; the survivors then go 32 / LMAX at a time, lane t
+// comparing survivor t / LMAX with link t mod LMAX's warp-wide box, and a
+// ballot leaves the (link, primitive) pairs whose boxes overlap; only those
+// take the exact ball test.  Both levels are conservative (the primitive
+// boxes carry a rounding margin, and the union holds every link box), so the
+// verdicts are those of testing every pair.  Returns the warp's stop
+// decision.
 template <int KIND, int MODE, bool STATS, int LMAX, bool SIMPLE, bool TEAM = false>
 __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *prims, const float4 *boxes, int n,
-                                          const LinkBox &lb, const Stash &stash, FrameCursor &fc, Ctl &ctl,
+                                          const WarpBoxes &wb, const Stash &stash, FrameCursor &fc, Ctl &ctl,
                                           bool &col, const WorkRef<STATS> &w, const Team &team = Team{}) {
     using K = Kind<KIND>;
     constexpr int PB = 32 / LMAX > 0 ? 32 / LMAX : 1;  // primitives per batch
@@ -530,69 +573,80 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
     const int lane = threadIdx.x & 31;
     const int my_l = lane % LMAX, my_p = lane / LMAX;
     const bool my_on = my_p < PB && ((P.link_mask >> my_l) & 1u);
-    const int k_first = TEAM ? team.part * PB : 0, k_step = TEAM ? team.nparts * PB : PB;
+    const int k_first = TEAM ? team.part * 32 : 0, k_step = TEAM ? team.nparts * 32 : 32;
 #pragma unroll 1
     for (int k0 = k_first; k0 < n; k0 += k_step) {
         if (TEAM && *team.flag) return true;  // another warp of the team found a collision
-        const int kb = k0 + my_p;
-        bool ov = false;
-        if (my_on && kb < n) {
-            const float4 lo = boxes[2 * kb], hi = boxes[2 * kb + 1];
-            ov = (lo.x <= lb.hx) & (hi.x >= lb.lx) & (lo.y <= lb.hy) & (hi.y >= lb.ly) & (lo.z <= lb.hz) &
-                 (hi.z >= lb.lz);
+        bool ou = false;
+        if (k0 + lane < n) {
+            ou = box_hits(boxes[2 * (k0 + lane)], boxes[2 * (k0 + lane) + 1], wb.all);
             w.slot(VP_WORK_BOX_TESTS, 1);
         }
-        unsigned m = __ballot_sync(kFull, ov);
-        while (m) {  // warp-uniform: primitives of the batch with an overlapping link
-            const int p = (__ffs(m) - 1) / LMAX;
-            const unsigned lm = (m >> (p * LMAX)) & kLinks;
-            m &= ~(kLinks << (p * LMAX));
-            const int k = k0 + p;
-            float4 o[K::kWords];
+#pragma unroll 1
+        for (unsigned mu = __ballot_sync(kFull, ou); mu;) {  // warp-uniform: the batch's survivors
+            int sel = -1;  // survivor my_p of the next PB, as an index into the batch
 #pragma unroll
-            for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
-            unsigned bits = 0;
-#pragma unroll 1
-            for (unsigned t = lm; t; t &= t - 1) {  // the links that survived the cull
-                const int l = __ffs(t) - 1;
-                bits |= static_cast<unsigned>(K::hit(stash.centre(l), P.links[l].bs.w, o)) << l;
+            for (int i = 0; i < PB; ++i) {
+                if (i == my_p && mu) sel = __ffs(mu) - 1;
+                mu &= mu - 1;
             }
-            w.slot(VP_WORK_LANE_COARSE, __popc(lm));
-            if (!ctl.idle) w.add(K::kCoarse, __popc(lm));
-            if (ctl.idle) bits = 0;
-            unsigned any = __reduce_or_sync(kFull, bits);
-            while (any) {
-                const int l = __ffs(any) - 1;
-                any &= any - 1;
-                const LinkC &L = P.links[l];
-                const Fr &f = frame_at<SIMPLE>(P, l, stash, fc);
-                const bool h = (bits >> l) & 1u;
-                float4 ol[K::kWords];  // the primitive in the link's frame: spheres tested in local coordinates
-                K::to_frame(f, o, ol);
-                // a link split in halves: each half's bounding sphere first; a
-                // half no lane touches is skipped by the whole warp
-                int a0 = L.s0, a1 = L.s1;
-                bool hA = h, hB = h;
-                if (L.sm < L.s1) {
-                    const float4 g0 = P.halves[l][0], g1 = P.halves[l][1];
-                    hA = h && K::hit(make_float3(g0.x, g0.y, g0.z), g0.w, ol);
-                    hB = h && K::hit(make_float3(g1.x, g1.y, g1.z), g1.w, ol);
-                    w.slot(VP_WORK_LANE_COARSE, 2);
-                    if (!ctl.idle) w.add(K::kCoarse, 2);
-                    if (!__any_sync(kFull, hA)) a0 = L.sm;
-                    if (!__any_sync(kFull, hB)) a1 = L.sm;
-                }
-                w.slot(VP_WORK_LANE_FINE, a1 - a0);
-                if (!ctl.idle) w.add(K::kFine, a1 - a0);
-                if (STATS) w.add(VP_WORK_FINE_OWN, (hA ? max(0, L.sm - a0) : 0) + (hB ? max(0, a1 - L.sm) : 0));
+            bool ov = false;
+            if (my_on && sel >= 0) {
+                ov = box_hits(boxes[2 * (k0 + sel)], boxes[2 * (k0 + sel) + 1], wb.link);
+                w.slot(VP_WORK_BOX_TESTS, 1);
+            }
+            unsigned m = __ballot_sync(kFull, ov);
+            while (m) {  // warp-uniform: survivors with an overlapping link
+                const int p = (__ffs(m) - 1) / LMAX;
+                const unsigned lm = (m >> (p * LMAX)) & kLinks;
+                m &= ~(kLinks << (p * LMAX));
+                const int k = k0 + __shfl_sync(kFull, sel, p * LMAX);
+                float4 o[K::kWords];
+#pragma unroll
+                for (int i = 0; i < K::kWords; ++i) o[i] = prims[k * K::kWords + i];
+                unsigned bits = 0;
 #pragma unroll 1
-                for (int s = a0; s < a1; ++s) {
-                    const float4 sp = P.spheres[s];
-                    col |= (s < L.sm ? hA : hB) && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
+                for (unsigned t = lm; t; t &= t - 1) {  // the links that survived the cull
+                    const int l = __ffs(t) - 1;
+                    bits |= static_cast<unsigned>(K::hit(stash.centre(l), P.links[l].bs.w, o)) << l;
                 }
-                if (group_stop<MODE>(ctl, col)) {
-                    if (TEAM && (threadIdx.x & 31) == 0) *team.flag = 1;
-                    return true;
+                w.slot(VP_WORK_LANE_COARSE, __popc(lm));
+                if (!ctl.idle) w.add(K::kCoarse, __popc(lm));
+                if (ctl.idle) bits = 0;
+                unsigned any = __reduce_or_sync(kFull, bits);
+                while (any) {
+                    const int l = __ffs(any) - 1;
+                    any &= any - 1;
+                    const LinkC &L = P.links[l];
+                    const Fr &f = frame_at<SIMPLE>(P, l, stash, fc);
+                    const bool h = (bits >> l) & 1u;
+                    float4 ol[K::kWords];  // the primitive in the link's frame: spheres tested in local coordinates
+                    K::to_frame(f, o, ol);
+                    // a link split in halves: each half's bounding sphere first; a
+                    // half no lane touches is skipped by the whole warp
+                    int a0 = L.s0, a1 = L.s1;
+                    bool hA = h, hB = h;
+                    if (L.sm < L.s1) {
+                        const float4 g0 = P.halves[l][0], g1 = P.halves[l][1];
+                        hA = h && K::hit(make_float3(g0.x, g0.y, g0.z), g0.w, ol);
+                        hB = h && K::hit(make_float3(g1.x, g1.y, g1.z), g1.w, ol);
+                        w.slot(VP_WORK_LANE_COARSE, 2);
+                        if (!ctl.idle) w.add(K::kCoarse, 2);
+                        if (!__any_sync(kFull, hA)) a0 = L.sm;
+                        if (!__any_sync(kFull, hB)) a1 = L.sm;
+                    }
+                    w.slot(VP_WORK_LANE_FINE, a1 - a0);
+                    if (!ctl.idle) w.add(K::kFine, a1 - a0);
+                    if (STATS) w.add(VP_WORK_FINE_OWN, (hA ? max(0, L.sm - a0) : 0) + (hB ? max(0, a1 - L.sm) : 0));
+#pragma unroll 1
+                    for (int s = a0; s < a1; ++s) {
+                        const float4 sp = P.spheres[s];
+                        col |= (s < L.sm ? hA : hB) && K::hit(make_float3(sp.x, sp.y, sp.z), sp.w, ol);
+                    }
+                    if (group_stop<MODE>(ctl, col)) {
+                        if (TEAM && (threadIdx.x & 31) == 0) *team.flag = 1;
+                        return true;
+                    }
                 }
             }
         }
@@ -620,9 +674,7 @@ __device__ __forceinline__ bool link_prim_pass(const RobotParams &P, int l, cons
         const int kb = k0 + lane;
         bool ov = false;
         if (kb < n) {
-            const float4 lo = boxes[2 * kb], hi = boxes[2 * kb + 1];
-            ov = (lo.x <= lb.hx) & (hi.x >= lb.lx) & (lo.y <= lb.hy) & (hi.y >= lb.ly) & (lo.z <= lb.hz) &
-                 (hi.z >= lb.lz);
+            ov = box_hits(boxes[2 * kb], boxes[2 * kb + 1], lb);
             w.slot(VP_WORK_BOX_TESTS, 1);
         }
         unsigned m = __ballot_sync(kFull, ov);
@@ -694,7 +746,7 @@ __device__ __forceinline__ bool pose_and_check_interleaved(const RobotParams &P,
             else if (pm != kParentPrev)
                 recompute_frame_cached<SIMPLE>(P, (J.meta >> kMetaParentLinkShift) & 0xFF, stash, f);
             float ms, mc;
-            joint_motion(J, qf(l - 1), ms, mc);
+            joint_motion_check(J, qf(l - 1), ms, mc);
             stash.mo(l - 1, 0) = ms;
             stash.mo(l - 1, 1) = mc;
             apply_joint_sc<SIMPLE>(J, ms, mc, f);
@@ -874,20 +926,20 @@ __device__ __forceinline__ bool pose_and_check_frequent(const RobotParams &P, co
 #pragma unroll 1
         for (int l = 0; l < P.n_links; ++l)
             if (((P.link_mask >> l) & 1u) && !((lp.centred >> l) & 1u)) ensure_link<SIMPLE>(P, l, qf, stash, lp, w);
-        const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
+        const WarpBoxes wb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
         FrameCursor fc;
 #pragma unroll 1
         for (int ki = 0; ki < 3; ++ki) {
             const int kind = (env.kind_order >> (4 * ki)) & 15;
             bool stop;
             if (kind == 0)
-                stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc, ctl, col,
+                stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE>(P, env.sph, env.bb_sph, env.ns, wb, stash, fc, ctl, col,
                                                             w);
             else if (kind == 1)
-                stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc, ctl, col,
+                stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE>(P, env.cap, env.bb_cap, env.nc, wb, stash, fc, ctl, col,
                                                             w);
             else
-                stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, lb, stash, fc, ctl, col,
+                stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE>(P, env.box, env.bb_box, env.nb, wb, stash, fc, ctl, col,
                                                             w);
             if (stop) return col;
         }
@@ -933,7 +985,7 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
                 else if (pm != kParentPrev)
                     recompute_frame_cached<SIMPLE>(P, (J.meta >> kMetaParentLinkShift) & 0xFF, stash, f);
                 float ms, mc;
-                joint_motion(J, qf(l - 1), ms, mc);
+                joint_motion_check(J, qf(l - 1), ms, mc);
                 stash.mo(l - 1, 0) = ms;
                 stash.mo(l - 1, 1) = mc;
                 apply_joint_sc<SIMPLE>(J, ms, mc, f);
@@ -987,19 +1039,19 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
                 }
             }
         } else {  // primitives
-            const LinkBox lb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
+            const WarpBoxes wb = warp_link_boxes<LMAX>(P, stash, !ctl.idle);
             FrameCursor fc;
             for (int ki = 0; ki < 3; ++ki) {
                 const int kind = (env.kind_order >> (4 * ki)) & 15;
                 bool stop;
                 if (kind == 0)
-                    stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.sph, env.bb_sph, env.ns, lb, stash, fc,
+                    stop = prim_pass<0, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.sph, env.bb_sph, env.ns, wb, stash, fc,
                                                                       ctl, col, w, team);
                 else if (kind == 1)
-                    stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.cap, env.bb_cap, env.nc, lb, stash, fc,
+                    stop = prim_pass<1, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.cap, env.bb_cap, env.nc, wb, stash, fc,
                                                                       ctl, col, w, team);
                 else
-                    stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.box, env.bb_box, env.nb, lb, stash, fc,
+                    stop = prim_pass<2, MODE, STATS, LMAX, SIMPLE, TEAM>(P, env.box, env.bb_box, env.nb, wb, stash, fc,
                                                                       ctl, col, w, team);
                 if (stop) return col;
             }

@@ -109,6 +109,24 @@ def test_state_verdicts(vpmod, name):
     assert 0 < got.mean() < 1 or big
 
 
+@pytest.mark.parametrize("name", [vpgen.TORSO8_OBB60_CAP20, vpgen.DUAL14_SHELVES])
+def test_state_verdicts_wrapped_angles(vpmod, name):
+    """The checks reduce each revolute angle to [-pi, pi] before the fast
+    sine and cosine: the same configurations turned by whole turns (up to
+    three either way, per joint) keep every pinned verdict of the oracle,
+    which takes sin and cos of the unreduced angle in FP64."""
+    w, val, o = _setup(vpmod, name, 64)
+    q = vpgen.uniform_configs(w.robot, 3001, seed=47 + vpgen.NAMES.index(name))
+    turns = np.random.default_rng(48).integers(-3, 4, size=q.shape)
+    turns[:, w.robot.joint_type == vpgen.PRISMATIC] = 0
+    qw = (q.astype(np.float64) + 2.0 * np.pi * turns).astype(np.float32)
+    assert np.abs(qw).max() > 6 * np.pi
+    got, K, pinned, bad = _compare_states(val, o, qw)
+    assert bad.size == 0, f"{bad.size} pinned states disagree"
+    assert pinned.mean() > 0.99
+    assert 0 < got.mean() < 1
+
+
 def _compare_edges(w, val, o, idx, mode, n_edges=None):
     from paper_2309_14545_gb300 import vp
     q0, q1 = _cuda(w.q0), _cuda(w.q1)
