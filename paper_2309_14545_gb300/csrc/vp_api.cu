@@ -50,6 +50,11 @@ struct vp_ctx {
     uint8_t *hx_valid = nullptr;
     size_t hx_cap_q = 0, hx_cap_e = 0;
     cudaStream_t hx_in = nullptr, hx_out = nullptr;
+    // batched chunks alternate between two compute streams, each with its
+    // own bucketing scratch, so that one chunk's persistent launch fills the
+    // SMs the previous one's tail leaves idle
+    cudaStream_t hx_cs[2] = {};
+    BatchedState hx_slot[2];
     cudaEvent_t hx_ev[2 * 8 + 2] = {};
     size_t rrt_node_cap = 0, rrt_parent_cap = 0, rrt_pending_cap = 0;
     FkCodegen fk_gen;            // per-robot FK compiled at run time (vp_fk_codegen)
@@ -142,6 +147,9 @@ extern "C" vp_status vp_destroy(vp_ctx *ctx) {
         if (ctx->env_buf) cudaFree(ctx->env_buf);
         if (ctx->status) cudaFree(ctx->status);
         batched_release(ctx->batched);
+        for (BatchedState &bs : ctx->hx_slot) batched_release(bs);
+        for (cudaStream_t cs : ctx->hx_cs)
+            if (cs) cudaStreamDestroy(cs);
         if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
         if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
         if (ctx->sc_q0) cudaFree(ctx->sc_q0);
@@ -649,7 +657,7 @@ extern "C" vp_status vp_edge_counts(vp_ctx *ctx, const float *q0, const float *q
 
 static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                                      float resolution, int64_t n_edges, uint8_t *valid, int mode,
-                                     uint64_t *work, void *stream) {
+                                     uint64_t *work, void *stream, BatchedState *slot = nullptr) {
     vp_status s = check_loaded(ctx);
     if (s != VP_OK) return s;
     if (n_edges < 0) return fail(ctx, VP_ERR_ARG, "n_edges < 0");
@@ -672,8 +680,9 @@ static vp_status validate_edges_impl(vp_ctx *ctx, const float *q0, const float *
             a.ev_stop = ctx->ev_stop;
         }
         std::string msg;
-        const int rc = work ? batched_work(ctx->batched, a, reinterpret_cast<unsigned long long *>(work), &msg)
-                            : batched_validate(ctx->batched, a, &msg);
+        BatchedState &bs = slot ? *slot : ctx->batched;
+        const int rc = work ? batched_work(bs, a, reinterpret_cast<unsigned long long *>(work), &msg)
+                            : batched_validate(bs, a, &msg);
         if (rc == 0) return VP_OK;
         return fail(ctx, rc == 1 ? VP_ERR_CAPACITY : VP_ERR_CUDA, "batched: %s", msg.c_str());
     }
@@ -755,22 +764,25 @@ extern "C" vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const 
     }
     if (!ctx->hx_in) e = cudaStreamCreateWithFlags(&ctx->hx_in, cudaStreamNonBlocking);
     if (e == cudaSuccess && !ctx->hx_out) e = cudaStreamCreateWithFlags(&ctx->hx_out, cudaStreamNonBlocking);
+    for (cudaStream_t &cs : ctx->hx_cs)
+        if (e == cudaSuccess && !cs) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     for (cudaEvent_t &ev : ctx->hx_ev)
         if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "vp_validate_edges_host (streams)");
     // chunks: the copies of chunk i+1 overlap the validation of chunk i, and
     // each chunk's verdicts go back as soon as they are known.  The plain
-    // kernel takes chunks of about 2^19 edges (at most 8).  Each batched
-    // launch costs about half a millisecond beyond its edges (the bucketing,
-    // and the persistent kernels' start and tail), so a large batch goes in
-    // two: a quarter, validated while the other three quarters are copied,
-    // then the rest.
+    // kernel takes chunks of about 2^19 edges (at most 8).  A batched chunk
+    // runs on one of two compute streams with its own scratch, so its
+    // persistent launch starts on the SMs the previous chunk's tail frees; a
+    // large batch goes in doubling chunks (1/16, 1/16, 1/8, 1/4, 1/2), the
+    // first copied in a sixteenth of the time of the whole.
     int64_t bounds[9] = {0};
     int n_chunks = 1;
     if (mode == VP_MODE_BATCHED) {
         if (n_edges >= (int64_t{1} << 20)) {
-            bounds[1] = n_edges / 4;
-            n_chunks = 2;
+            const int64_t parts[5] = {1, 2, 4, 8, 16};  // bounds in sixteenths
+            for (int c = 0; c < 5; ++c) bounds[c + 1] = n_edges * parts[c] / 16;
+            n_chunks = 5;
         }
     } else {
         n_chunks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, (n_edges + (1 << 19) - 1) >> 19)));
@@ -794,13 +806,20 @@ extern "C" vp_status vp_validate_edges_host(vp_ctx *ctx, const float *q0, const 
         if (e == cudaSuccess && counts)
             e = cudaMemcpyAsync(ctx->hx_counts + off, counts + off, n * sizeof(int32_t), cudaMemcpyHostToDevice,
                                 ctx->hx_in);
+        const bool batched = mode == VP_MODE_BATCHED;
+        cudaStream_t cs = batched ? ctx->hx_cs[c & 1] : st;
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], ctx->hx_in);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in[c], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[c], 0);
         if (e != cudaSuccess) break;
+        BatchedState *slot = nullptr;
+        if (batched) {
+            slot = &ctx->hx_slot[c & 1];
+            batched_mirror(*slot, ctx->batched);
+        }
         rs = validate_edges_impl(ctx, ctx->hx_q0 + qo, ctx->hx_q1 + qo, counts ? ctx->hx_counts + off : nullptr,
-                                 resolution, n, ctx->hx_valid + off, mode, nullptr, stream);
+                                 resolution, n, ctx->hx_valid + off, mode, nullptr, cs, slot);
         if (rs != VP_OK) break;
-        e = cudaEventRecord(ev_out[c], st);
+        e = cudaEventRecord(ev_out[c], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->hx_out, ev_out[c], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(valid + off, ctx->hx_valid + off, n, cudaMemcpyDeviceToHost, ctx->hx_out);

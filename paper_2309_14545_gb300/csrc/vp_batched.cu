@@ -152,6 +152,8 @@ struct Impl {
     int screen_rounds = kDefaultScreenRounds;
     int order = 0;  // check order (kOrder* bits)
     bool tuned = false;
+    uint64_t epoch = 0;          // graphs dropped so far (any change of robot, environment or tuning)
+    uint64_t mirrored = ~0ull;   // the source's epoch this state last copied (batched_mirror)
 };
 
 Impl *impl_of(BatchedState &st) {
@@ -165,6 +167,7 @@ void drop_graph(Impl *im) {
     for (auto &g : im->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     im->graphs.clear();
+    ++im->epoch;
 }
 
 int set_err(std::string *msg, const char *what, cudaError_t e) {
@@ -583,6 +586,20 @@ void batched_release(BatchedState &st) {
     if (im->cap_stream) cudaStreamDestroy(im->cap_stream);
     delete im;
     st.impl = nullptr;
+}
+
+void batched_mirror(BatchedState &dst, BatchedState &src) {
+    dst.watchdog_ns = src.watchdog_ns;  // part of each graph's key
+    Impl *d = impl_of(dst), *s = impl_of(src);
+    bool same = d->mirrored == s->epoch && d->screen_rounds == s->screen_rounds && d->order == s->order;
+    for (int b = 0; b < kNB; ++b) same = same && d->G[b] == s->G[b];
+    if (same) return;
+    for (int b = 0; b < kNB; ++b) d->G[b] = s->G[b];
+    d->screen_rounds = s->screen_rounds;
+    d->order = s->order;
+    d->tuned = s->tuned;
+    drop_graph(d);
+    d->mirrored = s->epoch;
 }
 
 void batched_set_screen_rounds(BatchedState &st, int rounds) {

@@ -84,6 +84,11 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg);
 // Batched validation without the graph, adding work counters into `work`.
 int batched_work(BatchedState &st, const BatchedArgs &a, unsigned long long *work, std::string *msg);
 void batched_invalidate(BatchedState &st);
+// Make dst validate as src does (its tiling, screening rounds and check
+// order), dropping dst's graphs whenever src's have been dropped since the
+// last call (a new robot, environment or tuning).  Another state's scratch
+// lets a second batch run beside the first, as the host-buffer call's chunks do.
+void batched_mirror(BatchedState &dst, BatchedState &src);
 void batched_release(BatchedState &st);
 // Lanes per edge chosen for each length bucket; returns the bucket count.
 int batched_tiling(const BatchedState &st, int *G, int n);
