@@ -256,9 +256,10 @@ def parse():
     ap.add_argument("--screen", type=int, default=None, help="pin the screening rounds (with --tiling)")
     ap.add_argument("--leg", default=None, choices=["grads", "nearest", "shortcut", "rrt", "fk"],
                     help="run only this secondary leg and print its result (for profiling one kernel)")
-    ap.add_argument("--check-order", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--check-order", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="pin the check order (bit 1: primitives before self pairs; bit 2: checks interleaved "
-                         "with posing; 4: frequent link pairs first); with --tiling, or in plain mode")
+                         "with posing; 4: frequent link pairs first; 5: the same in two passes over the batch); "
+                         "with --tiling, or in plain mode")
     return ap.parse_args()
 
 

@@ -319,14 +319,22 @@ vp_status vp_screen_rounds(vp_ctx *ctx, int *rounds);
  *   that hold three quarters of the counted collisions -- with each link
  *   posed only when a check first needs it; then primitives; then the
  *   remaining link pairs.
+ * VP_ORDER_FREQUENT_TWO_PASS (5): the frequent-first order over a whole
+ *   batch in two passes (VP_MODE_BATCHED; elsewhere as 4).  The first pass
+ *   checks only the leading link pairs on each edge's first-round states;
+ *   a second pass takes the edges left undecided and checks the rest on
+ *   those states, so that the rest runs in full warps instead of in the
+ *   few lanes of a warp whose other edges have already collided.
  * 0 (the default) is "pose all, self pairs first".  Which order finds a
  * colliding configuration with the least work depends on the robot and the
- * scene; vp_autotune times all five.  vp_set_check_order pins one
- * (VP_ERR_ARG outside 0..4) until the next vp_autotune or load.  The
- * verdicts do not depend on it. */
+ * scene; vp_autotune times all six.  vp_set_check_order pins one
+ * (VP_ERR_ARG outside 0..5) until the next vp_autotune or load.  The
+ * verdicts do not depend on it, except for states within rounding of
+ * contact: the orders rebuild link frames along different float paths. */
 #define VP_ORDER_PRIMS_FIRST 0x1
 #define VP_ORDER_INTERLEAVE 0x2
 #define VP_ORDER_FREQUENT 0x4
+#define VP_ORDER_FREQUENT_TWO_PASS 5
 vp_status vp_set_check_order(vp_ctx *ctx, int order);
 vp_status vp_check_order(vp_ctx *ctx, int *order);
 

@@ -100,10 +100,11 @@ class Validator:
 
     def check_order(self):
         """The check order: VP_ORDER_FREQUENT (4: the link pairs that
-        collide most often first, links posed on demand), or VP_ORDER_*
-        bits: 1 if primitives are checked before self pairs, plus 2 if each
-        link is checked as soon as it is posed (else every link is posed
-        first)."""
+        collide most often first, links posed on demand),
+        VP_ORDER_FREQUENT_TWO_PASS (5: the same in two passes over a batched
+        call, the leading pairs of every edge first), or VP_ORDER_* bits: 1
+        if primitives are checked before self pairs, plus 2 if each link is
+        checked as soon as it is posed (else every link is posed first)."""
         return vp.vp_check_order(self.ctx)
 
     def set_check_order(self, order):

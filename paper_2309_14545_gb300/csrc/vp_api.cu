@@ -998,7 +998,7 @@ vp_status vp_link_bounds(vp_ctx *ctx, int n_links, float *link_sphere, float *ha
 
 extern "C" vp_status vp_set_check_order(vp_ctx *ctx, int order) {
     if (!ctx) return VP_ERR_ARG;
-    if (order < 0 || order >= kOrderCount) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 to 4");
+    if (order < 0 || order >= kOrderCount) return fail(ctx, VP_ERR_ARG, "vp_set_check_order: 0 to 5");
     batched_set_check_order(ctx->batched, order);
     return VP_OK;
 }

@@ -109,7 +109,7 @@ SurvivorsKernel survivors_kernel_for(const RobotParams &P, bool stats, bool stag
 
 size_t batched_smem(const EnvView &env, const RobotParams &P) {
     return env_smem_bytes(env) + 16 + static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float) +
-           static_cast<size_t>(P.n_links * kCentreFloats + P.n_joints * 2) * kBlock * sizeof(float);
+           static_cast<size_t>(stash_floats(P.n_links)) * kBlock * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +133,7 @@ struct Impl {
     int32_t *kbuf = nullptr;  // state count per edge (-1: answered in the bucketing pass)
     int2 *perm = nullptr;     // (edge, count) bucket by bucket, longest bucket first
     int2 *surv = nullptr;     // (edge, count) of the edges left to the second phase
+    int2 *defer = nullptr;    // (edge, count) a two-pass order's first pass deferred, in perm's bucket ranges
     int *ctrl = nullptr;
     int64_t cap = 0;
     cudaStream_t cap_stream = nullptr;
@@ -189,14 +190,17 @@ int ensure_capacity(Impl *im, int64_t E, std::string *msg) {
     if (im->kbuf) cudaFree(im->kbuf);
     if (im->perm) cudaFree(im->perm);
     if (im->surv) cudaFree(im->surv);
+    if (im->defer) cudaFree(im->defer);
     im->kbuf = nullptr;
     im->perm = nullptr;
     im->surv = nullptr;
+    im->defer = nullptr;
     im->cap = 0;
     const int64_t n = std::max<int64_t>(E, 1 << 16);
     cudaError_t e = cudaMalloc(&im->kbuf, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&im->perm, n * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&im->surv, n * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&im->defer, n * sizeof(int2));
     if (e != cudaSuccess) return set_err(msg, "cudaMalloc scratch", e);
     im->cap = n;
     return 0;
@@ -255,6 +259,28 @@ int prepare_kernel(const BatchedArgs &a, EnvView *view, size_t *smem, int *grid,
     return 0;
 }
 
+// The screening launch: one pass, or for the two-pass order the leading
+// link pairs of every edge's first-round states, then the rest of the
+// checks on the edges that left undecided (the first pass's list in place
+// of perm).
+cudaError_t launch_screening(Impl *im, const RobotParams &P, const EnvView &view, BatchPlan plan, const float *q0,
+                             const float *q1, int grid, size_t smem, cudaStream_t s, uint8_t *valid,
+                             unsigned *status, unsigned long long *work) {
+    const BatchedKernel k = batched_kernel_for(P, work != nullptr, view.staged, view.order);
+    if (view.order != kOrderTwoPass) {
+        plan.pass = 0;
+        k<<<grid, kBlock, smem, s>>>(P, view, q0, q1, im->perm, plan, valid, status, im->ctrl, im->surv, im->defer,
+                                     work);
+        return cudaGetLastError();
+    }
+    plan.pass = 1;
+    k<<<grid, kBlock, smem, s>>>(P, view, q0, q1, im->perm, plan, valid, status, im->ctrl, im->surv, im->defer, work);
+    plan.pass = 2;
+    k<<<grid, kBlock, smem, s>>>(P, view, q0, q1, im->defer, plan, valid, status, im->ctrl, im->surv, im->defer,
+                                 work);
+    return cudaGetLastError();
+}
+
 // Enqueue the whole pipeline on stream s (also used under capture).
 cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const BatchPlan &plan, size_t smem, int grid,
                     cudaStream_t s, uint8_t *valid, unsigned long long *work = nullptr) {
@@ -267,10 +293,7 @@ cudaError_t enqueue(Impl *im, const BatchedArgs &a, const EnvView &view, const B
     // external event-record nodes, so the events time the kernel when replayed from the graph
     if (a.ev_start) e = cudaEventRecordWithFlags(a.ev_start, s, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    batched_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
-                                                                            plan, valid, a.status, im->ctrl, im->surv,
-                                                                            work);
-    e = cudaGetLastError();
+    e = launch_screening(im, *a.robot, view, plan, a.q0, a.q1, grid, smem, s, valid, a.status, work);
     if (e != cudaSuccess) return e;
     survivors_kernel_for(*a.robot, work != nullptr, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
                                                                               plan, valid, a.status, im->ctrl, work);
@@ -453,12 +476,11 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     auto time_plan = [&](float *ms_out) {
         float best = 1e30f;
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, 3 * sizeof(int), s);  // both queues, survivor count
+            // the queues, the survivor count and the deferred counts
+            e = cudaMemsetAsync(im->ctrl + kCtrlQueue, 0, kCtrlQueueInts * sizeof(int), s);
             if (e != cudaSuccess) break;
             cudaEventRecord(t0, s);
-            batched_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->perm,
-                                                                           p, tv, a.status, im->ctrl, im->surv,
-                                                                           nullptr);
+            launch_screening(im, *a.robot, view, p, a.q0, a.q1, grid, smem, s, tv, a.status, nullptr);
             survivors_kernel_for(*a.robot, false, view.staged, view.order)<<<grid, kBlock, smem, s>>>(*a.robot, view, a.q0, a.q1, im->surv,
                                                                              p, tv, a.status, im->ctrl, nullptr);
             cudaEventRecord(t1, s);

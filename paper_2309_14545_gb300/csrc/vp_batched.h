@@ -18,6 +18,9 @@ constexpr int kCtrlCursor = 16;  // ctrl[16..24] scatter cursors
 constexpr int kCtrlQueue = 32;   // ctrl[32]     work-item counter
 constexpr int kCtrlSurv = 33;    // ctrl[33]     edges left to the second phase
 constexpr int kCtrlQueue2 = 34;  // ctrl[34]     second-phase work-item counter
+constexpr int kCtrlQueueB = 35;  // ctrl[35]     work-item counter of a two-pass order's second pass
+constexpr int kCtrlDefer = 36;   // ctrl[36..44] edges per bucket the first pass left undecided
+constexpr int kCtrlQueueInts = 13;  // ctrl[32..44]: the counters each screening run starts from zero
 constexpr int kCtrlInts = 64;
 constexpr int kSplit = 16;       // second-phase work items per edge
 constexpr int kDefaultScreenRounds = 0;
@@ -27,6 +30,8 @@ struct BatchPlan {
     int edge_lo[kNB], edge_hi[kNB];  // bucket b's edges are perm[edge_lo[b], edge_hi[b]) (when !from_hist)
     int from_hist;         // 1: offsets from the histogram in ctrl (longest bucket first)
     int screen_rounds;     // rounds a lane group spends on an edge before handing it on (0: no limit)
+    int pass;              // 0: one screening pass; two-pass order: 1, the leading link pairs of the
+                           // first-round states, undecided edges deferred by bucket; 2, the deferred edges
     unsigned long long watchdog_ns;  // time budget of one launch
 };
 
@@ -35,7 +40,7 @@ struct BatchPlan {
 using PlainKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int32_t *, float, long long,
                              uint8_t *, unsigned *, unsigned long long *);
 using BatchedKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
-                               uint8_t *, unsigned *, int *, int2 *, unsigned long long *);
+                               uint8_t *, unsigned *, int *, int2 *, int2 *, unsigned long long *);
 using SurvivorsKernel = void (*)(RobotParams, EnvView, const float *, const float *, const int2 *, BatchPlan,
                                  uint8_t *, unsigned *, int *, unsigned long long *);
 struct KernelSet {

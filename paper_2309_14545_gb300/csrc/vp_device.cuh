@@ -326,6 +326,17 @@ __device__ __forceinline__ void recompute_frame_cached(const RobotParams &P, int
     }
 }
 
+// The validation stash for n_links links and `stride` threads laid out at p
+// (stash_floats(n_links) * stride floats); no frame slots.
+__device__ __forceinline__ Stash stash_at(unsigned char *p, int n_links, int stride) {
+    Stash st;
+    st.frames = nullptr;
+    st.centres = reinterpret_cast<float *>(p);
+    st.motion = st.centres + static_cast<size_t>(n_links) * kCentreFloats * stride;
+    st.stride = stride;
+    return st;
+}
+
 // A link frame kept between requests: the frame of the last link asked for,
 // and the joints on its path.  A request for a descendant link (whose path
 // contains the kept one) only applies the joints past it -- joints are
@@ -902,21 +913,37 @@ __device__ __forceinline__ bool frequent_groups(const RobotParams &P, int gi0, i
 // collides there poses only those links' paths; then, if the state is still
 // free, every remaining link is posed and the primitives are checked as in
 // pose_and_check_all; then the remaining link pairs.  Verdicts equal those
-// of the other orders.
+// of the other orders.  Only phases first_phase .. last_phase run (a state
+// checked in two parts is counted once, in the part with phase 0).
 template <int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
 __device__ __forceinline__ bool pose_and_check_frequent(const RobotParams &P, const QF &qf, const EnvSm &env,
                                                         const Stash &stash, const Ctl &ctl_in,
-                                                        const WorkRef<STATS> &w) {
+                                                        const WorkRef<STATS> &w, int first_phase = 0,
+                                                        int last_phase = 2) {
     bool col = false;
     Ctl ctl = ctl_in;
-    w.add(VP_WORK_STATES, 1);
-    w.slot(VP_WORK_LANE_STATES, 1);
+    if (first_phase == 0) {
+        w.add(VP_WORK_STATES, 1);
+        w.slot(VP_WORK_LANE_STATES, 1);
+    }
     LazyPose lp;
     FrameCursor cur_a, cur_b;
+    if (first_phase > 0) {
+        // the poses phase 0 leaves, by the same calls in the same order, so
+        // that a state checked in two parts gets the values of one check
+        // (phase 0 ran to its end: the state had not collided there)
+        const WorkRef<STATS> wz{w.w, false};
+#pragma unroll 1
+        for (int gi = 0; gi < P.n_gfront; ++gi) {
+            const GroupC G = P.groups[P.gorder[gi]];
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) ensure_link<SIMPLE>(P, side ? G.lb : G.la, qf, stash, lp, wz);
+        }
+    }
     // phase 0: the leading link pairs; 1: primitives; 2: the other link
     // pairs (one loop, so that the group code is laid out once)
 #pragma unroll 1
-    for (int phase = 0; phase < 3; ++phase) {
+    for (int phase = first_phase; phase <= last_phase; ++phase) {
         if (phase != 1) {
             const int g0 = phase == 0 ? 0 : P.n_gfront, g1 = phase == 0 ? P.n_gfront : P.n_groups;
             if (frequent_groups<MODE, STATS, SIMPLE>(P, g0, g1, qf, stash, lp, cur_a, cur_b, ctl, col, w)) return col;
@@ -1066,16 +1093,20 @@ __device__ __forceinline__ bool pose_and_check_all(const RobotParams &P, const Q
 enum : int { kFamPoseAll = 0, kFamInterleave = 1, kFamFrequent = 2, kFamCount = 3 };
 
 __host__ __device__ __forceinline__ int family_of(int order) {
-    return order == kOrderFrequent ? kFamFrequent : ((order & kOrderInterleave) ? kFamInterleave : kFamPoseAll);
+    return (order & kOrderFrequent) ? kFamFrequent : ((order & kOrderInterleave) ? kFamInterleave : kFamPoseAll);
 }
 
 // One state checked in the order of family FAM (the prims-first bit of
 // env.order still applies within it).
+// The frequent-first family runs its phases first_phase .. last_phase only
+// (the two-pass order's passes); the others ignore them.
 template <int FAM, int MODE, bool STATS, int LMAX, bool SIMPLE, class QF>
 __device__ __forceinline__ bool check_state(const RobotParams &P, const QF &qf, const EnvSm &env, const Stash &stash,
-                                            const Ctl &ctl, const WorkRef<STATS> &w) {
+                                            const Ctl &ctl, const WorkRef<STATS> &w, int first_phase = 0,
+                                            int last_phase = 2) {
     if constexpr (FAM == kFamFrequent)
-        return pose_and_check_frequent<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
+        return pose_and_check_frequent<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w, first_phase,
+                                                                  last_phase);
     else if constexpr (FAM == kFamInterleave)
         return pose_and_check_interleaved<MODE, STATS, LMAX, SIMPLE>(P, qf, env, stash, ctl, w);
     else

@@ -35,6 +35,10 @@ constexpr int kMetaParentLinkShift = 16;  // 8 bits: the parent link's index
 constexpr int kFrameFloats = 12;   // frame [R row-major | p] of a branch-point link
 constexpr int kCentreFloats = 3;   // world centre of a link's bounding sphere
 
+// Per-lane floats of the validation stash for n links: each link's centre,
+// then each joint's motion parameters (sin q, cos q).
+__host__ __device__ constexpr int stash_floats(int n_links) { return n_links * kCentreFloats + (n_links - 1) * 2; }
+
 // Conservative inflation of every link bounding sphere (m): covers float32
 // rounding in the coarse test so a coarse miss never hides a fine hit.
 constexpr float kCoarseEps = 1e-5f;
@@ -107,9 +111,11 @@ struct EnvView {
 constexpr int kOrderPrimsFirst = VP_ORDER_PRIMS_FIRST;
 constexpr int kOrderInterleave = VP_ORDER_INTERLEAVE;
 // Self-pair groups most often colliding first (RobotParams::gorder), each
-// link posed when a check first needs it, then primitives.
+// link posed when a check first needs it, then primitives; 5 is the same in
+// two passes over a batch (the leading groups of every edge first).
 constexpr int kOrderFrequent = VP_ORDER_FREQUENT;
-constexpr int kOrderCount = 5;
+constexpr int kOrderTwoPass = VP_ORDER_FREQUENT_TWO_PASS;
+constexpr int kOrderCount = 6;
 
 // Dynamic shared memory the environment takes in a block.
 __host__ __device__ inline size_t env_smem_bytes(const EnvView &env) {

@@ -60,11 +60,7 @@ __device__ __forceinline__ SmemCarve carve(unsigned char *smem, const EnvView &e
     off += 16;
     c.warp_buf = reinterpret_cast<float *>(smem + off);
     off += static_cast<size_t>((blockDim.x + 31) / 32) * 32 * sizeof(float);
-    c.stash.frames = nullptr;
-    c.stash.centres = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_links) * kCentreFloats * blockDim.x * sizeof(float);
-    c.stash.motion = reinterpret_cast<float *>(smem + off);
-    c.stash.stride = static_cast<int>(blockDim.x);
+    c.stash = stash_at(smem + off, P.n_links, static_cast<int>(blockDim.x));
     return c;
 }
 
@@ -170,7 +166,7 @@ template <bool STATS, int LMAX, bool SIMPLE, bool STAGED, int FAM>
 __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
     const __grid_constant__ RobotParams P, const EnvView env, const float *__restrict__ q0,
     const float *__restrict__ q1, const int2 *__restrict__ perm, const BatchPlan plan, uint8_t *__restrict__ valid,
-    unsigned *status, int *ctrl, int2 *__restrict__ surv, unsigned long long *work) {
+    unsigned *status, int *ctrl, int2 *__restrict__ surv, int2 *defer, unsigned long long *work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_edge_lo[kNB], s_edge_hi[kNB], s_item_end[kNB];
     __shared__ int s_items;
@@ -180,12 +176,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
     off += 16;
     float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
     off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
-    Stash stash;
-    stash.frames = nullptr;
-    stash.centres = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_links) * kCentreFloats * kBlock * sizeof(float);
-    stash.motion = reinterpret_cast<float *>(smem + off);
-    stash.stride = kBlock;
+    const Stash stash = stash_at(smem + off, P.n_links, kBlock);
 
     if (threadIdx.x == 0) {
         int eo[kNB + 1];
@@ -201,6 +192,10 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
                 s_edge_hi[b] = plan.edge_hi[b];
             }
         }
+        // a second pass takes the edges the first one deferred, which it
+        // wrote from the start of each bucket's range (perm is that list)
+        if (plan.pass == 2)
+            for (int b = 0; b < kNB; ++b) s_edge_hi[b] = s_edge_lo[b] + ctrl[kCtrlDefer + b];
         // work items in processing order: longest bucket first
         int items = 0;
         for (int b = kNB - 1; b >= 0; --b) {
@@ -230,7 +225,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
                 atomicOr(status, VP_DEVERR_TIMEOUT);
                 item = -1;
             } else {
-                item = atomicAdd(&ctrl[kCtrlQueue], 1);
+                item = atomicAdd(&ctrl[plan.pass == 2 ? kCtrlQueueB : kCtrlQueue], 1);
             }
         }
         item = __shfl_sync(kFull, item, 0);
@@ -275,17 +270,25 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         const int R = (k + G - 1) / G;
         const float inv = __fdiv_rn(1.f, static_cast<float>(k - 1));
         const int R_max = __reduce_max_sync(kFull, has_edge && group_fin ? R : 0);
-        const int R_lim = plan.screen_rounds > 0 ? min(R_max, plan.screen_rounds) : R_max;
+        // the first of two passes checks the first round's states against
+        // the leading link pairs only (check phase 0); the second checks the
+        // rest of them on the same states (the bucket, and so the lanes per
+        // edge, is the same), then goes on as a single pass does
+        const int R_lim = plan.pass == 1 ? min(R_max, 1)
+                                         : (plan.screen_rounds > 0 ? min(R_max, plan.screen_rounds) : R_max);
+        const int last_phase = plan.pass == 1 ? 0 : 2;
         bool done = !has_edge || !group_fin;
         for (int r = 0; r < R_lim; ++r) {
             int i = j * R + r;
             const WorkRef<STATS> w{&wk, !done && i < k};
             if (i >= k) i = k - 1;
             const float t = static_cast<float>(i) * inv;
+            const int first_phase = plan.pass == 2 && r == 0 ? 1 : 0;
             const bool c = check_state<FAM, kStopGroups, STATS, LMAX, SIMPLE>(
-                P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w);
+                P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w,
+                first_phase, last_phase);
             const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
-            if (!done && (gcol || r == R - 1)) {
+            if (!done && (gcol || (plan.pass != 1 && r == R - 1))) {
                 if (j == 0) {
                     valid[e] = gcol ? 0 : 1;
                     if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
@@ -295,11 +298,16 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
             if (__all_sync(kFull, done)) break;
         }
         // an edge the screening rounds left undecided goes to the second phase
-        // (valid until one of its work items there finds a collision)
+        // (valid until one of its work items there finds a collision); one
+        // the first of two passes left undecided, to the second pass
         if (!done && j == 0) {
-            surv[atomicAdd(&ctrl[kCtrlSurv], 1)] = make_int2(e, k);
-            valid[e] = 1;
-            if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
+            if (plan.pass == 1) {
+                defer[s_edge_lo[b] + atomicAdd(&ctrl[kCtrlDefer + b], 1)] = make_int2(e, k);
+            } else {
+                surv[atomicAdd(&ctrl[kCtrlSurv], 1)] = make_int2(e, k);
+                valid[e] = 1;
+                if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
+            }
         }
         if constexpr (STATS) {
 #pragma unroll
@@ -333,12 +341,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) survivors_kernel(
     off += 16;
     float *gbuf = reinterpret_cast<float *>(smem + off);  // [warps][8 groups][32]
     off += static_cast<size_t>(kBlock / 32) * 8 * 32 * sizeof(float);
-    Stash stash;
-    stash.frames = nullptr;
-    stash.centres = reinterpret_cast<float *>(smem + off);
-    off += static_cast<size_t>(P.n_links) * kCentreFloats * kBlock * sizeof(float);
-    stash.motion = reinterpret_cast<float *>(smem + off);
-    stash.stride = kBlock;
+    const Stash stash = stash_at(smem + off, P.n_links, kBlock);
     if (STAGED && !stage_env(env_sm, env, bar, status)) return;
     const EnvSm es = env_views<STAGED>(env_sm, env);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

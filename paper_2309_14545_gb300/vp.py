@@ -22,6 +22,7 @@ STATUS_NAMES = ["VP_OK", "VP_ERR_ARG", "VP_ERR_CUDA", "VP_ERR_CAPACITY", "VP_ERR
 VP_MODE_PLAIN, VP_MODE_BATCHED, VP_MODE_PER_EDGE = 0, 1, 2
 VP_DEVERR_COUNT, VP_DEVERR_LENGTH, VP_DEVERR_TIMEOUT = 0x1, 0x2, 0x4
 VP_ORDER_PRIMS_FIRST, VP_ORDER_INTERLEAVE, VP_ORDER_FREQUENT = 0x1, 0x2, 0x4
+VP_ORDER_FREQUENT_TWO_PASS = 5
 VP_MAX_JOINTS, VP_MAX_SPHERES, VP_MAX_PAIRS = 16, 256, 1024
 VP_MAX_ENV_BYTES = 160 * 1024
 VP_NOALLOC_MAX_ENV_BYTES = 64 * 1024

@@ -26,11 +26,36 @@ def _cuda(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def _same_outside_band(w, got, want, idx=None):
+    """Verdicts of two check orders: both families pose the links with the
+    same arithmetic but rebuild link frames along different float paths, so
+    they may differ only where the oracle puts the edge in the boundary band
+    (some state within 1e-4 m of contact)."""
+    diff = np.nonzero(got != want)[0]
+    if diff.size == 0:
+        return 0
+    o = oracle.Oracle(w.robot, w.env)
+    e = diff if idx is None else idx[diff]
+    c = None if w.counts is None else w.counts[e]
+    cls, _ = o.classify_edges(w.q0[e], w.q1[e], c, w.res)
+    assert np.all(cls == 2), f"{int((cls != 2).sum())} edges outside the band differ"
+    return int(diff.size)
+
+
+def _same_states_outside_band(w, q, got, want):
+    diff = np.nonzero(got != want)[0]
+    if diff.size == 0:
+        return 0
+    K = oracle.Oracle(w.robot, w.env).clearance(q[diff].astype(np.float64))
+    assert np.all(np.abs(K) <= oracle.BAND), f"{int((np.abs(K) > oracle.BAND).sum())} states outside the band differ"
+    return int(diff.size)
+
+
 def _both(val, vp, w, tune):
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
-    plain = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
-    if tune:
+    if tune:  # the tuned check order is the plain kernel's too
         val.autotune(q0, q1, c, float(w.res))
+    plain = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
     out = torch.full((w.q0.shape[0],), 9, dtype=torch.uint8, device="cuda")
     val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
     first = out.cpu().numpy()
@@ -148,50 +173,62 @@ def test_batched_work_counters(vpmod):
                                     (vpgen.ARM7_SPHERES16, 30_000)])
 def test_second_phase_matches_plain(vpmod, name, n):
     """Edges handed to the second launch (after 1, 2 or 4 screening rounds,
-    or none) get the verdicts of the plain kernel, at several tilings."""
+    or none) get the verdicts of the plain kernel, at several tilings, in the
+    default order and in the two-pass order (whose first pass hands edges to
+    a second screening launch as well)."""
     Validator, vp = vpmod
     w = vpgen.workload(name, n_edges=n)
     val = Validator(w.robot, w.env)
     q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
     want = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
     assert 0 < want.mean() < 1
-    for rounds in (1, 2, 4, 0):
-        val.set_screen_rounds(rounds)
-        assert val.screen_rounds() == rounds
-        for lanes in ([4] * 9, [32] * 9, [4, 8, 16, 8, 4, 16, 8, 32, 16]):
-            val.set_tiling(lanes)
-            out = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
-            val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
-            assert np.array_equal(out.cpu().numpy(), want), (rounds, lanes)
+    for order in (0, vp.VP_ORDER_FREQUENT_TWO_PASS):
+        val.set_check_order(order)
+        want_o = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+        for rounds in (1, 2, 4, 0):
+            val.set_screen_rounds(rounds)
+            assert val.screen_rounds() == rounds
+            for lanes in ([4] * 9, [32] * 9, [4, 8, 16, 8, 4, 16, 8, 32, 16]):
+                val.set_tiling(lanes)
+                out = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+                val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED, out=out)
+                assert np.array_equal(out.cpu().numpy(), want_o), (order, rounds, lanes)
+    val.set_check_order(0)
     # the other check orders (primitives first; checks interleaved with
     # posing, either way round; frequent link pairs first with links posed
-    # on demand): the same verdicts in both modes, and for states
+    # on demand): within one order every mode and setting gives the same
+    # verdicts bit for bit; across orders they agree outside the band
     states = q0[: min(n, 20000)]
     want_s = val.validate_states(states).cpu().numpy()
-    for order in (1, 2, 3, 4):
+    qs = w.q0[: min(n, 20000)]
+    for order in (1, 2, 3, 4, 5):
         val.set_check_order(order)
         assert val.check_order() == order
-        for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
-            got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
-            assert np.array_equal(got, want), (order, mode)
+        ref = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+        ndiff = _same_outside_band(w, ref, want)
+        got = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+        assert np.array_equal(got, ref), order
         got, work = val.validate_edges_work(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED)
-        assert np.array_equal(got.cpu().numpy(), want), order
+        assert np.array_equal(got.cpu().numpy(), ref), order
         assert int(work[vp.VP_WORK_EDGES_DONE]) == n
-        assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s), order
+        nds = _same_states_outside_band(w, qs, val.validate_states(states).cpu().numpy(), want_s)
+        print(f"{name} order {order}: {ndiff} band edges and {nds} band states differ from order 0")
     val.set_check_order(0)
     assert val.sync_status()[0] == vp.VP_OK
     with pytest.raises(vp.VPError):
         val.set_screen_rounds(-1)
-    for bad in (-1, 5):
+    for bad in (-1, 6):
         with pytest.raises(vp.VPError):
             val.set_check_order(bad)
     # the frequent-first order after the tuner has counted the groups
     val.autotune(q0, q1, c, float(w.res))
-    val.set_check_order(4)
-    for mode in (vp.VP_MODE_PLAIN, vp.VP_MODE_BATCHED):
-        got = val.validate_edges(q0, q1, c, float(w.res), mode=mode).cpu().numpy()
-        assert np.array_equal(got, want), ("tuned 4", mode)
-    assert np.array_equal(val.validate_states(states).cpu().numpy(), want_s)
+    for order in (4, 5):
+        val.set_check_order(order)
+        ref = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+        _same_outside_band(w, ref, want)
+        got = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+        assert np.array_equal(got, ref), ("tuned", order)
+        _same_states_outside_band(w, qs, val.validate_states(states).cpu().numpy(), want_s)
     val.close()
 
 
