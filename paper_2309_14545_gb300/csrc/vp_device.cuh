@@ -871,16 +871,20 @@ __device__ __forceinline__ void ensure_link(const RobotParams &P, int l, const Q
 }
 
 // Self-pair groups gorder[gi0 .. gi1) for the frequent-first order, each
-// link posed when a group first needs it.  Returns the warp's stop decision.
+// link posed when a group first needs it (pose_only: the posing alone,
+// uncounted).  Returns the warp's stop decision.
 template <int MODE, bool STATS, bool SIMPLE, class QF>
 __device__ __forceinline__ bool frequent_groups(const RobotParams &P, int gi0, int gi1, const QF &qf,
                                                 const Stash &stash, LazyPose &lp, FrameCursor &cur_a,
-                                                FrameCursor &cur_b, Ctl &ctl, bool &col, const WorkRef<STATS> &w) {
+                                                FrameCursor &cur_b, Ctl &ctl, bool &col, const WorkRef<STATS> &w,
+                                                bool pose_only = false) {
+    const WorkRef<STATS> wp{w.w, w.real && !pose_only};
 #pragma unroll 1
     for (int gi = gi0; gi < gi1; ++gi) {
         const GroupC G = P.groups[P.gorder[gi]];
 #pragma unroll 1
-        for (int side = 0; side < 2; ++side) ensure_link<SIMPLE>(P, side ? G.lb : G.la, qf, stash, lp, w);
+        for (int side = 0; side < 2; ++side) ensure_link<SIMPLE>(P, side ? G.lb : G.la, qf, stash, lp, wp);
+        if (pose_only) continue;
         const float3 ca = stash.centre(G.la), cb = stash.centre(G.lb);
         const float dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
         const float rr = P.links[G.la].bs.w + P.links[G.lb].bs.w;
@@ -928,25 +932,18 @@ __device__ __forceinline__ bool pose_and_check_frequent(const RobotParams &P, co
     }
     LazyPose lp;
     FrameCursor cur_a, cur_b;
-    if (first_phase > 0) {
-        // the poses phase 0 leaves, by the same calls in the same order, so
-        // that a state checked in two parts gets the values of one check
-        // (phase 0 ran to its end: the state had not collided there)
-        const WorkRef<STATS> wz{w.w, false};
-#pragma unroll 1
-        for (int gi = 0; gi < P.n_gfront; ++gi) {
-            const GroupC G = P.groups[P.gorder[gi]];
-#pragma unroll 1
-            for (int side = 0; side < 2; ++side) ensure_link<SIMPLE>(P, side ? G.lb : G.la, qf, stash, lp, wz);
-        }
-    }
     // phase 0: the leading link pairs; 1: primitives; 2: the other link
-    // pairs (one loop, so that the group code is laid out once)
+    // pairs (one loop, so that the group code is laid out once).  A state's
+    // second part (first_phase > 0) still walks phase 0, posing only: the
+    // same posing calls in the same order give it the values of one check
+    // (phase 0 ran to its end there, since the state had not collided).
 #pragma unroll 1
-    for (int phase = first_phase; phase <= last_phase; ++phase) {
+    for (int phase = 0; phase <= last_phase; ++phase) {
         if (phase != 1) {
             const int g0 = phase == 0 ? 0 : P.n_gfront, g1 = phase == 0 ? P.n_gfront : P.n_groups;
-            if (frequent_groups<MODE, STATS, SIMPLE>(P, g0, g1, qf, stash, lp, cur_a, cur_b, ctl, col, w)) return col;
+            if (frequent_groups<MODE, STATS, SIMPLE>(P, g0, g1, qf, stash, lp, cur_a, cur_b, ctl, col, w,
+                                                     phase < first_phase))
+                return col;
             continue;
         }
         // primitives: every sphere-carrying link posed, then as pose_and_check_all

@@ -169,6 +169,9 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
     unsigned *status, int *ctrl, int2 *__restrict__ surv, int2 *defer, unsigned long long *work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_edge_lo[kNB], s_edge_hi[kNB], s_item_end[kNB];
+    // the two-pass order is one of the frequent-first family's: the other
+    // families' instances compile the single pass only
+    const int pass = FAM == kFamFrequent ? plan.pass : 0;
     __shared__ int s_items;
     size_t off = STAGED ? static_cast<size_t>(env.n_float4) * 16 : 0;
     float4 *env_sm = reinterpret_cast<float4 *>(smem);
@@ -194,7 +197,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         }
         // a second pass takes the edges the first one deferred, which it
         // wrote from the start of each bucket's range (perm is that list)
-        if (plan.pass == 2)
+        if (pass == 2)
             for (int b = 0; b < kNB; ++b) s_edge_hi[b] = s_edge_lo[b] + ctrl[kCtrlDefer + b];
         // work items in processing order: longest bucket first
         int items = 0;
@@ -225,7 +228,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
                 atomicOr(status, VP_DEVERR_TIMEOUT);
                 item = -1;
             } else {
-                item = atomicAdd(&ctrl[plan.pass == 2 ? kCtrlQueueB : kCtrlQueue], 1);
+                item = atomicAdd(&ctrl[pass == 2 ? kCtrlQueueB : kCtrlQueue], 1);
             }
         }
         item = __shfl_sync(kFull, item, 0);
@@ -274,21 +277,21 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         // the leading link pairs only (check phase 0); the second checks the
         // rest of them on the same states (the bucket, and so the lanes per
         // edge, is the same), then goes on as a single pass does
-        const int R_lim = plan.pass == 1 ? min(R_max, 1)
+        const int R_lim = pass == 1 ? min(R_max, 1)
                                          : (plan.screen_rounds > 0 ? min(R_max, plan.screen_rounds) : R_max);
-        const int last_phase = plan.pass == 1 ? 0 : 2;
+        const int last_phase = pass == 1 ? 0 : 2;
         bool done = !has_edge || !group_fin;
         for (int r = 0; r < R_lim; ++r) {
             int i = j * R + r;
             const WorkRef<STATS> w{&wk, !done && i < k};
             if (i >= k) i = k - 1;
             const float t = static_cast<float>(i) * inv;
-            const int first_phase = plan.pass == 2 && r == 0 ? 1 : 0;
+            const int first_phase = pass == 2 && r == 0 ? 1 : 0;
             const bool c = check_state<FAM, kStopGroups, STATS, LMAX, SIMPLE>(
                 P, [t, gq0, gdq](int jj) { return fmaf(t, gdq[jj], gq0[jj]); }, es, stash, Ctl{gmask, done}, w,
                 first_phase, last_phase);
             const bool gcol = (__ballot_sync(kFull, c && !done) & gmask) != 0u;
-            if (!done && (gcol || (plan.pass != 1 && r == R - 1))) {
+            if (!done && (gcol || (pass != 1 && r == R - 1))) {
                 if (j == 0) {
                     valid[e] = gcol ? 0 : 1;
                     if (STATS) wk.v[VP_WORK_EDGES_DONE] += 1;
@@ -301,7 +304,7 @@ __global__ void VP_VALIDATION_BOUNDS(LMAX, 6) edges_batched_kernel(
         // (valid until one of its work items there finds a collision); one
         // the first of two passes left undecided, to the second pass
         if (!done && j == 0) {
-            if (plan.pass == 1) {
+            if (pass == 1) {
                 defer[s_edge_lo[b] + atomicAdd(&ctrl[kCtrlDefer + b], 1)] = make_int2(e, k);
             } else {
                 surv[atomicAdd(&ctrl[kCtrlSurv], 1)] = make_int2(e, k);
