@@ -758,8 +758,10 @@ def grads_leg(dev, flush, stream):
 
 
 def _traffic(args, E, mode):
-    """DRAM bytes per launch from the committed ncu summary, only if it was
-    taken on the current kernel sources (else null)."""
+    """DRAM bytes of the edge kernel's launches in one step (both passes of
+    the two-pass order) from the committed ncu summary, scaled per edge to
+    this batch; only if it was taken on the current kernel sources (else
+    null)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -771,7 +773,7 @@ def _traffic(args, E, mode):
         ent = rec.get(f"{args.workload}-{'batched' if mode == 1 else 'plain'}")
         if not ent:
             return None
-        return float(ent["dram_bytes_per_launch"]) * E / float(ent["edges"])
+        return float(ent["dram_bytes_per_step"]) * E / float(ent["edges"])
     except Exception:
         return None
 

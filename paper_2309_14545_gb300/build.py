@@ -31,7 +31,8 @@ def _deps():
 
 # The files that define the edge-validation kernels (device code, tables and
 # their layouts); host-side launch code, the tuner and other kernels are not.
-KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_inst.cu", "vp_api.cu")
+KERNEL_FILES = ("vp_types.h", "vp_device.cuh", "vp_validate.cuh", "vp_batched.h", "vp_batched.cu", "vp_inst.cu",
+                "vp_api.cu")
 
 # vp_inst.cu holds the validation kernels of one link bound and one family of
 # check orders per compilation: it is compiled once for each pair.
