@@ -501,45 +501,33 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
     float cur = 0.f;
     time_plan(&cur);  // warm-up
     time_plan(&cur);
-    // screening rounds (0: no second phase), with the other choices held
-    auto tune_screen = [&]() {
-        const int keep = p.screen_rounds;
-        int best_r = keep;
+    // check order (self pairs or primitives first; every link posed first,
+    // or checks interleaved with posing; frequent pairs first, in one pass
+    // or two) together with the screening rounds, the tiling held: the
+    // two interact (a two-pass order wants a short screen), so one at a
+    // time can stop short of the best pair
+    auto tune_order = [&]() {
+        const int keep_o = view.order, keep_r = p.screen_rounds;
+        int best_o = keep_o, best_r = keep_r;
         float best = cur;
-        for (int R : {1, 2, 4, 8, 0}) {
-            if (R == keep || e != cudaSuccess) continue;
-            p.screen_rounds = R;
-            float ms = 0.f;
-            time_plan(&ms);
-            if (ms < 0.99f * best) {
-                best = ms;
-                best_r = R;
+        for (int o = 0; o < kOrderCount && e == cudaSuccess; ++o)
+            for (int R : {1, 2, 4, 8, 0}) {
+                if ((o == keep_o && R == keep_r) || e != cudaSuccess) continue;
+                view.order = o;
+                p.screen_rounds = R;
+                float ms = 0.f;
+                time_plan(&ms);
+                if (e == cudaSuccess && ms < 0.99f * best) {
+                    best = ms;
+                    best_o = o;
+                    best_r = R;
+                }
             }
-        }
+        view.order = best_o;
         p.screen_rounds = best_r;
         cur = best;
     };
-    // check order (self pairs or primitives first; every link posed first,
-    // or checks interleaved with posing), the other choices held
-    auto tune_order = [&]() {
-        const int keep = view.order;
-        int best_o = keep;
-        float best = cur;
-        for (int o = 0; o < kOrderCount && e == cudaSuccess; ++o) {
-            if (o == keep) continue;
-            view.order = o;
-            float ms = 0.f;
-            time_plan(&ms);
-            if (e == cudaSuccess && ms < 0.99f * best) {
-                best = ms;
-                best_o = o;
-            }
-        }
-        view.order = best_o;
-        cur = best;
-    };
     tune_order();
-    tune_screen();
     const int options[4] = {4, 8, 16, 32};
     bool moved = true;
     for (int pass = 0; pass < 3 && moved && e == cudaSuccess; ++pass) {
@@ -565,7 +553,6 @@ int batched_autotune(BatchedState &st, const BatchedArgs &a, std::string *msg) {
             cur = best;
         }
     }
-    if (e == cudaSuccess) tune_screen();
     if (e == cudaSuccess) tune_order();
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
