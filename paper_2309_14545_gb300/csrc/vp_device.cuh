@@ -584,9 +584,12 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
     const int lane = threadIdx.x & 31;
     const int my_l = lane % LMAX, my_p = lane / LMAX;
     const bool my_on = my_p < PB && ((P.link_mask >> my_l) & 1u);
-    const int k_first = TEAM ? team.part * 32 : 0, k_step = TEAM ? team.nparts * 32 : 32;
+    // a team splits the second level: every warp of it checks the same
+    // states, so it sees the same survivors, and takes every nparts-th
+    // group of them (the first level is one ballot per 32 primitives)
+    int chunk = 0;
 #pragma unroll 1
-    for (int k0 = k_first; k0 < n; k0 += k_step) {
+    for (int k0 = 0; k0 < n; k0 += 32) {
         if (TEAM && *team.flag) return true;  // another warp of the team found a collision
         bool ou = false;
         if (k0 + lane < n) {
@@ -601,8 +604,10 @@ __device__ __forceinline__ bool prim_pass(const RobotParams &P, const float4 *pr
                 if (i == my_p && mu) sel = __ffs(mu) - 1;
                 mu &= mu - 1;
             }
+            const bool mine = !TEAM || chunk % team.nparts == team.part;
+            ++chunk;
             bool ov = false;
-            if (my_on && sel >= 0) {
+            if (mine && my_on && sel >= 0) {
                 ov = box_hits(boxes[2 * (k0 + sel)], boxes[2 * (k0 + sel) + 1], wb.link);
                 w.slot(VP_WORK_BOX_TESTS, 1);
             }
