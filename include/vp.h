@@ -465,8 +465,8 @@ vp_status vp_sync_status(vp_ctx *ctx, void *stream, uint32_t *bits);
  * Runs on the calling thread's current device.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and the
  * device's launch limits.  Every call copies the environment from pageable
- * host memory and synchronises `stream`, so a call cannot be recorded into
- * a CUDA graph by stream capture.  Every call shares the array and it keeps the previous call's contents:
+ * host memory and synchronises `stream`.  Every call shares the array and it
+ * keeps the previous call's contents:
  * each call restages the environment and clears the status word on
  * `stream` first.  Calls that overlap on the GPU (other host threads, other
  * streams) race on the array and must be serialised by the caller.
