@@ -88,15 +88,6 @@ __device__ __forceinline__ void joint_motion_check(const JointC &J, float q, flo
     }
 }
 
-// The same, out of line: the frequent-first order poses joints from more
-// than one place, and a single copy of the code there keeps the kernel's
-// instructions in cache (9% faster on 1,000 primitives with the accurate
-// sincosf; the pose-all and interleaved loops keep the inlined copy, which
-// they pose from once).
-static __device__ __noinline__ void joint_motion_outlined(const JointC &J, float q, float &s, float &c) {
-    joint_motion_check(J, q, s, c);
-}
-
 // f <- f * origin_j * M_j: one joint of the chain, from its motion
 // parameters (s, c) as given by joint_motion.  SIMPLE: the robot has only
 // canonical axes (x, y, z) and identity origin rotations, so the code for
@@ -857,7 +848,7 @@ __device__ __forceinline__ void ensure_link(const RobotParams &P, int l, const Q
             ms = stash.mo(j, 0);
             mc = stash.mo(j, 1);
         } else {
-            joint_motion_outlined(J, qf(j), ms, mc);
+            joint_motion_check(J, qf(j), ms, mc);
             stash.mo(j, 0) = ms;
             stash.mo(j, 1) = mc;
             lp.posed |= 1u << j;
