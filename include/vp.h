@@ -257,12 +257,13 @@ vp_status vp_collision_cost(vp_ctx *ctx, const float *q, int64_t n, float margin
  * the device).  First it counts, on the batch's first (up to) 65,536 start
  * configurations, how often each self-pair link pair and each primitive
  * collides with the robot, and orders both most often first: the link pairs
- * for VP_ORDER_FREQUENT, the primitives (within each kind, and the kinds by
- * their totals) for every check order -- a state that collides then meets
- * its collision sooner.  Then it chooses the tiling, the screening rounds and
- * the check order by timing whole launches.  The choice is cached in the
- * context per robot, environment and edge-length profile.  The verdicts do
- * not depend on any of it. */
+ * for the frequent-first orders (4 and 5), the primitives (within each kind,
+ * and the kinds by their totals) for every check order -- a state that
+ * collides then meets its collision sooner.  Then it chooses the tiling, and
+ * the check order together with the screening rounds, by timing whole
+ * launches.  The choice is cached in the context per robot, environment and
+ * edge-length profile.  The verdicts do not depend on any of it, except as
+ * vp_set_check_order describes for states within rounding of contact. */
 vp_status vp_autotune(vp_ctx *ctx, const float *q0, const float *q1, const int32_t *counts,
                       float resolution, int64_t n_edges, void *stream);
 
