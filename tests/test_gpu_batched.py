@@ -305,3 +305,41 @@ def test_watchdog_reports_timeout_and_context_survives(vpmod):
     assert np.array_equal(got, plain)
     with pytest.raises(vp.VPError):
         vp.vp_set_watchdog(val.ctx, -1.0)
+
+
+@pytest.mark.parametrize("case", ["no_self_pairs", "no_primitives"])
+def test_two_pass_order_edge_cases(vpmod, case):
+    """The two-pass order where its first pass decides nothing (a robot with
+    no self pairs: every edge is deferred) and where the second has no
+    primitives to check (an empty scene): batched verdicts equal the plain
+    kernel's at several tilings and screening rounds, and pinned edges of a
+    subset match the oracle."""
+    import dataclasses
+    from robots_small import EMPTY_ENV
+    Validator, vp = vpmod
+    w = vpgen.workload(vpgen.DUAL14_MIXED1000, n_edges=40_000)
+    robot, env = w.robot, w.env
+    if case == "no_self_pairs":
+        robot = dataclasses.replace(robot, self_pairs=np.zeros((0, 2), dtype=np.int32))
+    else:
+        env = EMPTY_ENV
+    val = Validator(robot, env)
+    q0, q1, c = _cuda(w.q0), _cuda(w.q1), _cuda(w.counts)
+    val.autotune(q0, q1, c, float(w.res))
+    val.set_check_order(vp.VP_ORDER_FREQUENT_TWO_PASS)
+    want = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_PLAIN).cpu().numpy()
+    for rounds in (1, 0):
+        val.set_screen_rounds(rounds)
+        for lanes in ([4] * 9, [4, 8, 16, 32, 32, 32, 32, 32, 32]):
+            val.set_tiling(lanes)
+            got = val.validate_edges(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED).cpu().numpy()
+            assert np.array_equal(got, want), (case, rounds, lanes)
+    got, work = val.validate_edges_work(q0, q1, c, float(w.res), mode=vp.VP_MODE_BATCHED)
+    assert np.array_equal(got.cpu().numpy(), want)
+    assert int(work[vp.VP_WORK_EDGES_DONE]) == w.q0.shape[0]
+    assert val.sync_status()[0] == vp.VP_OK
+    idx = np.arange(0, w.q0.shape[0], 80)
+    cls, _ = oracle.Oracle(robot, env).classify_edges(w.q0[idx], w.q1[idx], w.counts[idx], w.res)
+    pinned = cls != 2
+    assert np.array_equal(want[idx][pinned], (cls[pinned] == 0).astype(np.uint8))
+    val.close()
